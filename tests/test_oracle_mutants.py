@@ -1,0 +1,56 @@
+"""The oracle's pins reject planted mistakes.
+
+Each case copies ep_oracle.c, plants one plausible mistake (a dropped term, a
+flipped sign, a swapped index, a wrong coefficient), compiles the copy on the
+CPU and runs the pin suite against it in a subprocess.  The pins must fail for
+every mutant; otherwise the mistake would be invisible to them.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ep_oracle.c")
+
+MUTANTS = {
+    "rhs_dq_drops_self_term": (
+        "            for (int c = 0; c < dim; ++c) sq[c] += g * pj[c];\n            if (j != i) {",
+        "            if (j != i) for (int c = 0; c < dim; ++c) sq[c] += g * pj[c];\n            if (j != i) {"),
+    "rhs_dp_sign": ("sp[c] -= w * (qi[c] - qj[c]);", "sp[c] += w * (qi[c] - qj[c]);"),
+    "rhs_dp_uses_pi_twice": ("double w = dot(dim, pi, pj) * orc_phi", "double w = dot(dim, pi, pi) * orc_phi"),
+    "gauss_phi_power": ("return -orc_G(kernel, sigma, r) / (sigma * sigma);", "return -orc_G(kernel, sigma, r) / sigma;"),
+    "tent_phi_power": ("-1.0 / (sigma * r) : 0.0;", "-1.0 / (sigma * r * r) : 0.0;"),
+    "hamiltonian_half": ("    return 0.5 * total;", "    return total;"),
+    "rk4_weight": ("(k1q[a] + 2.0 * k2q[a] + 2.0 * k3q[a] + k4q[a])", "(k1q[a] + 2.0 * k2q[a] + 1.0 * k3q[a] + 2.0 * k4q[a])"),
+    "rk4_stage3_input": ("yq[a] = q[a] + 0.5 * dt * k2q[a];\n        yp[a] = p[a] + 0.5 * dt * k2p[a];",
+                         "yq[a] = q[a] + 0.5 * dt * k1q[a];\n        yp[a] = p[a] + 0.5 * dt * k2p[a];"),
+    "match_update_sign": ("p0[a] += h * (Y[a] - q1[a]);", "p0[a] -= h * (Y[a] - q1[a]);"),
+    "hvp_drops_psi": ("b * (phi * dv[c] + psi * ddv * d[c])", "b * (phi * dv[c])"),
+    "hvp_transposed_cross_term": ("double a = dot(dim, vpi, pj) + dot(dim, pi, vpj);",
+                                  "double a = dot(dim, vpj, pj) + dot(dim, pi, vpj);"),
+    "adjoint_stage_coeff": ("kb3q[a] += dt * yq[a]; kb3p[a] += dt * yp[a];",
+                            "kb3q[a] += 0.5 * dt * yq[a]; kb3p[a] += 0.5 * dt * yp[a];"),
+    "adjoint_drops_metric_term": ("grad[a] = k1q[a] + xbp[a];", "grad[a] = xbp[a];"),
+    "expcone_psi_term": ("(1.0 / (sigma * sigma * r * r) + 1.0 / (sigma * r * r * r))",
+                         "(1.0 / (sigma * sigma * r * r))"),
+    "cell_predicate_le": ("if (r2 < 1.0f) {", "if (r2 <= 1.1f) {"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique in ep_oracle.c"
+    mut = tmp_path / "ep_oracle_mut.c"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-std=c11", "-shared", "-fPIC",
+                    "-o", str(lib), str(mut), "-lm"], check=True)
+    env = dict(os.environ, EP_ORACLE_VARIANT_LIB=str(lib), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins accepted the mutant {name}:\n{r.stdout[-2000:]}"

@@ -1,0 +1,354 @@
+"""Pins of the FP64 CPU oracle against what arXiv 1510.03816 and the mathematics fix.
+
+None of these tests re-types the oracle's formulas: each one checks a
+property that a dropped term, a wrong sign, index or coefficient would break
+(finite differences of H, conservation laws, exact special cases, closed
+forms, and the Hamiltonian values the paper prints).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import quad, solve_ivp
+
+from oracle import oracle as o
+from paper_1510_03816_gb300 import workloads as w
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+KERNELS = [(o.GAUSS, 0.3), (o.TENT, 0.45), (o.EXPCONE, 0.4)]
+
+
+def _cloud(n, dim, seed, spread=1.0, pscale=0.3, min_gap=0.05, sigma=None, kernel=None):
+    """Random positions with all pair distances away from 0 and, for the tent, from its
+    kink at r = sigma."""
+    if kernel is not None and kernel != o.TENT:
+        sigma = None
+    rng = np.random.default_rng(seed)
+    for _ in range(1000):
+        q = rng.uniform(0, spread, size=(n, dim))
+        d = np.linalg.norm(q[:, None] - q[None], axis=-1)[np.triu_indices(n, 1)]
+        if d.min() < min_gap:
+            continue
+        if sigma is not None and np.min(np.abs(d - sigma)) < min_gap:
+            continue
+        return q, rng.normal(0, pscale, size=(n, dim))
+    raise RuntimeError("no admissible cloud")
+
+
+# --------------------------------------------------------------------------- kernel functors
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+def test_functors_closed_forms_and_derivatives(kernel, sigma):
+    # closed-form values
+    assert o.G(kernel, sigma, 0.0) == 1.0
+    if kernel == o.GAUSS:
+        assert math.isclose(o.G(kernel, sigma, sigma), math.exp(-0.5), rel_tol=1e-15)
+    elif kernel == o.TENT:
+        assert o.G(kernel, sigma, 0.5 * sigma) == 0.5
+        assert o.G(kernel, sigma, sigma) == 0.0 and o.G(kernel, sigma, 2 * sigma) == 0.0
+        assert o.phi(kernel, sigma, 1.5 * sigma) == 0.0 and o.psi(kernel, sigma, 1.5 * sigma) == 0.0
+    else:
+        assert math.isclose(o.G(kernel, sigma, sigma), math.exp(-1.0), rel_tol=1e-15)
+    # phi = G'/r and psi = phi'/r against central differences of G and phi
+    for r in np.linspace(0.1, 0.9, 7) * sigma:
+        h = 1e-6 * sigma
+        dG = (o.G(kernel, sigma, r + h) - o.G(kernel, sigma, r - h)) / (2 * h)
+        dphi = (o.phi(kernel, sigma, r + h) - o.phi(kernel, sigma, r - h)) / (2 * h)
+        assert math.isclose(o.phi(kernel, sigma, r), dG / r, rel_tol=1e-7)
+        assert math.isclose(o.psi(kernel, sigma, r), dphi / r, rel_tol=1e-6)
+
+
+# --------------------------------------------------------------------------- right-hand side
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rhs_is_symplectic_gradient_of_H(kernel, sigma, dim):
+    """Eq. N-particle is Hamiltonian (Eq. charsham): dq = dH/dp, dp = -dH/dq (FD of Eq. H)."""
+    q, p = _cloud(7, dim, seed=10 + dim + 3 * kernel, spread=0.6, sigma=sigma, kernel=kernel)
+    dq, dp = o.rhs(q, p, kernel, sigma)
+    h = 1e-6
+    for i in range(q.shape[0]):
+        for c in range(dim):
+            e = np.zeros_like(q)
+            e[i, c] = h
+            dHdp = (o.hamiltonian(q, p + e, kernel, sigma) - o.hamiltonian(q, p - e, kernel, sigma)) / (2 * h)
+            dHdq = (o.hamiltonian(q + e, p, kernel, sigma) - o.hamiltonian(q - e, p, kernel, sigma)) / (2 * h)
+            assert abs(dq[i, c] - dHdp) < 1e-8 * (1 + abs(dHdp))
+            assert abs(dp[i, c] + dHdq) < 1e-8 * (1 + abs(dHdq))
+
+
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rhs_momentum_and_angular_momentum_rates_vanish(kernel, sigma, dim):
+    q, p = _cloud(40, dim, seed=3, spread=1.0, min_gap=1e-3)
+    dq, dp = o.rhs(q, p, kernel, sigma)
+    scale = np.abs(dp).max() + np.abs(dq).max()
+    assert np.all(np.abs(dp.sum(0)) < 1e-13 * q.shape[0] * scale)
+    if dim == 2:
+        lrate = np.sum(q[:, 0] * dp[:, 1] - q[:, 1] * dp[:, 0] + dq[:, 0] * p[:, 1] - dq[:, 1] * p[:, 0])
+        assert abs(lrate) < 1e-12 * q.shape[0] * scale
+    else:
+        lrate = np.sum(np.cross(q, dp) + np.cross(dq, p), axis=0)
+        assert np.all(np.abs(lrate) < 1e-12 * q.shape[0] * scale)
+
+
+def test_rhs_self_term_and_isolated_particles():
+    """dq includes j = i with G(0) = 1, dp excludes it (Eq. N-particle)."""
+    q = np.array([[0.1, 0.2], [5.0, 5.0]])
+    p = np.array([[0.3, -0.7], [1.0, 2.0]])
+    dq, dp = o.rhs(q, p, o.TENT, 0.5)
+    np.testing.assert_array_equal(dq, p)
+    np.testing.assert_array_equal(dp, np.zeros_like(p))
+    # coincident distinct particles: tent/expcone take phi = 0 at r = 0
+    qc = np.array([[0.1, 0.2], [0.1, 0.2]])
+    for k in (o.TENT, o.EXPCONE, o.GAUSS):
+        dq, dp = o.rhs(qc, p, k, 0.5)
+        np.testing.assert_allclose(dq, np.array([p.sum(0), p.sum(0)]), rtol=0, atol=1e-15)
+        np.testing.assert_array_equal(dp, np.zeros_like(p))
+
+
+def test_rhs_two_particles_by_hand():
+    """Two particles, Gaussian: the sums of Eq. N-particle have two terms each."""
+    s = 0.7
+    q = np.array([[0.0, 0.0], [0.3, 0.4]])  # r = 0.5
+    p = np.array([[1.0, 2.0], [-0.5, 0.25]])
+    g = math.exp(-0.25 / (2 * s * s))
+    dq, dp = o.rhs(q, p, o.GAUSS, s)
+    np.testing.assert_allclose(dq[0], p[0] + g * p[1], rtol=1e-15)
+    # dp_0 = -(p0.p1) G'(r) (q0 - q1)/r with G'(r) = -r/s^2 G
+    pp = p[0] @ p[1]
+    np.testing.assert_allclose(dp[0], -pp * (-0.5 / s**2 * g) * (q[0] - q[1]) / 0.5, rtol=1e-14)
+    np.testing.assert_allclose(dp[1], -dp[0], rtol=1e-15)
+
+
+# --------------------------------------------------------------------------- RK4 shoot
+def _richardson(kernel, sigma, dim=2):
+    q, p = _cloud(8, dim, seed=21, spread=0.5, pscale=0.2, min_gap=0.02)
+    ref, _ = o.shoot(q, p, kernel, sigma, steps=512)
+    errs = [np.abs(o.shoot(q, p, kernel, sigma, steps=s)[0] - ref).max() for s in (8, 16, 32)]
+    return errs
+
+
+@pytest.mark.parametrize("kernel,sigma", [(o.GAUSS, 0.3), (o.EXPCONE, 0.4)])
+def test_rk4_is_fourth_order(kernel, sigma):
+    e8, e16, e32 = _richardson(kernel, sigma)
+    assert 12.0 < e8 / e16 < 20.0
+    assert 12.0 < e16 / e32 < 20.0
+
+
+def test_conservation_over_a_shoot():
+    """Sum p is conserved to rounding (linear invariant, preserved by RK4); H and
+    2-D angular momentum are conserved to O(dt^4)."""
+    q, p = _cloud(30, 2, seed=5, spread=0.8, pscale=0.1, min_gap=0.01)
+    k, s = o.GAUSS, 0.25
+    H0 = o.hamiltonian(q, p, k, s)
+    L0 = np.sum(q[:, 0] * p[:, 1] - q[:, 1] * p[:, 0])
+    errH, errL = [], []
+    for steps in (20, 40):
+        q1, p1 = o.shoot(q, p, k, s, steps)
+        np.testing.assert_allclose(p1.sum(0), p.sum(0), rtol=0, atol=1e-14)
+        errH.append(abs(o.hamiltonian(q1, p1, k, s) - H0))
+        errL.append(abs(np.sum(q1[:, 0] * p1[:, 1] - q1[:, 1] * p1[:, 0]) - L0))
+    assert errH[1] < 1e-6 * abs(H0) and errH[0] / errH[1] > 10
+    assert errL[1] < 1e-6 and errL[0] / max(errL[1], 1e-300) > 10
+
+
+def test_time_reversal():
+    q, p = _cloud(12, 2, seed=6, spread=0.6, pscale=0.2, min_gap=0.02)
+    for steps in (20, 40):
+        q1, p1 = o.shoot(q, p, o.GAUSS, 0.3, steps, t1=1.0)
+        qb, pb = o.shoot(q1, p1, o.GAUSS, 0.3, steps, t1=-1.0)
+        err = max(np.abs(qb - q).max(), np.abs(pb - p).max())
+        if steps == 20:
+            e20 = err
+    assert err < 1e-7 and e20 / err > 10
+
+
+def test_momentum_scaling_law():
+    """F(q, s p) = (s F_q, s^2 F_p), so RK4 with momentum s p0 over [0, 1] equals RK4
+    with p0 over [0, s] with the same number of steps (pins the t^2 law of the
+    Hamiltonian series of Sec. 7, Example 1)."""
+    q, p = _cloud(10, 2, seed=8, spread=0.6, pscale=0.2, min_gap=0.02)
+    for sc in (0.25, 0.6):
+        qa, pa = o.shoot(q, sc * p, o.EXPCONE, 0.5, 30, t1=1.0)
+        qb, pb = o.shoot(q, p, o.EXPCONE, 0.5, 30, t1=sc)
+        np.testing.assert_allclose(qa, qb, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(pa, sc * pb, rtol=0, atol=1e-13)
+        assert math.isclose(o.hamiltonian(q, sc * p, o.EXPCONE, 0.5),
+                            sc * sc * o.hamiltonian(q, p, o.EXPCONE, 0.5), rel_tol=1e-14)
+
+
+def test_single_particle_and_far_apart_tent_particles_move_straight():
+    X = np.array([[0.2, 0.3]])
+    p0 = np.array([[0.05, -0.02]])
+    q1, p1 = o.shoot(X, p0, o.GAUSS, 0.1, 7)
+    np.testing.assert_allclose(q1, X + p0, rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(p1, p0)
+    # tent: pairs always farther apart than sigma do not interact
+    Xf = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    pf = np.array([[0.1, 0.0], [0.0, 0.1], [-0.1, 0.0]])
+    q1, p1 = o.shoot(Xf, pf, o.TENT, 0.5, 9)
+    np.testing.assert_allclose(q1, Xf + pf, rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(p1, pf)
+
+
+def test_concentric_shoot_matches_one_dof_reduction():
+    """Radial momenta on N equispaced points keep the ring a circle; with P_R = N P the
+    reduced Hamiltonian is P_R^2 S(R) / (2N), S(R) = sum_k cos(2 pi k/N) G(2R |sin(pi k/N)|)."""
+    N, R0, P = 16, 1.0, 0.05
+    X, _ = w.concentric_circles(N, R0, R0)
+    p0 = P * X / R0
+    k = np.arange(N)
+    sig = 0.8
+
+    def S(R):
+        return np.sum(np.cos(2 * np.pi * k / N) * np.exp(-(2 * R * np.abs(np.sin(np.pi * k / N))) ** 2 / (2 * sig**2)))
+
+    def dS(R, h=1e-6):
+        return (S(R + h) - S(R - h)) / (2 * h)
+
+    def f(t, y):
+        R, PR = y
+        return [PR * S(R) / N, -PR * PR * dS(R) / (2 * N)]
+
+    sol = solve_ivp(f, (0, 1), [R0, N * P], rtol=1e-12, atol=1e-14)
+    q1, p1 = o.shoot(X, p0, o.GAUSS, sig, 100)
+    radii = np.linalg.norm(q1, axis=1)
+    np.testing.assert_allclose(radii, sol.y[0, -1], rtol=1e-8)
+    np.testing.assert_allclose(np.sum(p1 * q1 / radii[:, None], axis=1), sol.y[1, -1] / N, rtol=1e-6)
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+def _closed_form_H(N, R0, R1, G):
+    k = np.arange(N)
+
+    def S(R):
+        return np.sum(np.cos(2 * np.pi * k / N) * G(2 * R * np.abs(np.sin(np.pi * k / N))))
+
+    I = quad(lambda R: 1.0 / np.sqrt(S(R)), R0, R1, epsabs=1e-14, epsrel=1e-13)[0]
+    return 0.5 * N * I * I
+
+
+def test_match_concentric_circles_closed_form_and_paper_values():
+    """Sec. 9, Fig. H_distance (b),(c): circle r=2 -> r=1 and r=2 -> r=3, N=64, G = e^{-r}.
+    The converged H equals the 1-DOF quadrature (N/2)(int dR / sqrt(S(R)))^2, and the
+    paper's printed numbers equal E = 2H (Eq. E=2H) to the paper's eps = 1e-3."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_fig8_hamiltonian.json")))
+    N = gold["n"]
+    for case in gold["cases"]:
+        X, Y = w.concentric_circles(N, gold["reference_radius"], case["target_radius"])
+        p, st, it, res, hist = o.match(X, Y, o.EXPCONE, 1.0, 50, eps=1e-11, maxit=2000)
+        assert st == o.OK and res < 1e-11
+        H = o.hamiltonian(X, p, o.EXPCONE, 1.0)
+        Hc = _closed_form_H(N, gold["reference_radius"], case["target_radius"], lambda r: np.exp(-r))
+        assert math.isclose(H, Hc, rel_tol=1e-7)
+        assert math.isclose(2 * H, case["printed_H"], rel_tol=gold["rel_tol"])
+        # the residual history decreases monotonically for this contraction
+        assert np.all(np.diff(hist) < 0)
+
+
+def test_match_single_particle_unit_gain_converges_in_one_update():
+    X = np.array([[0.5, 0.5]])
+    Y = np.array([[0.53, 0.48]])
+    p, st, it, res, hist = o.match(X, Y, o.TENT, 0.25, 10, h=1.0, eps=1e-12)
+    assert st == o.OK and it == 1
+    np.testing.assert_allclose(p, Y - X, rtol=0, atol=1e-16)
+    assert hist[0] == pytest.approx(0.03)
+
+
+def test_match_update_rule_first_iterate():
+    """With p0 = 0 the first shoot leaves X in place, so p1 = h (Y - X) exactly."""
+    pr = w.circle_to_ellipse(16)
+    h = 0.05
+    p, st, it, res, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, 5, h=h, eps=0.0, maxit=1)
+    assert st == o.ENOTCONVERGED and it == 1
+    np.testing.assert_allclose(p, h * (pr.Y - pr.X), rtol=0, atol=1e-17)
+    assert hist[0] == pytest.approx(np.abs(pr.Y - pr.X).max(), rel=1e-15)
+
+
+def test_match_reports_divergence():
+    """Too large a gain blows up (Table 2, h > 1: NaN); the oracle reports it as a status."""
+    pr = w.circle_to_ellipse(32)
+    p, st, it, res, hist = o.match(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=50.0, eps=1e-6, maxit=200)
+    assert st in (o.EDIVERGED, o.ENOTCONVERGED)
+    assert st == o.EDIVERGED or hist[-1] > 1e3 * hist[0]
+
+
+def test_iso_invariance_of_H():
+    """Table 4: H is invariant under rotation, translation and reflection of both templates,
+    and p0 transforms covariantly (rotated/reflected with the landmarks)."""
+    pr = w.circle_to_ellipse(24)
+    k, s = o.EXPCONE, 0.1
+    p, st, it, res, _ = o.match(pr.X, pr.Y, k, s, 10, h=0.5, eps=1e-12, maxit=3000)
+    assert st == o.OK
+    H = o.hamiltonian(pr.X, p, k, s)
+    th = math.pi / 3
+    Rm = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    Fm = np.array([[1.0, 0.0], [0.0, -1.0]])
+    for A, b in ((Rm, 0.0), (np.eye(2), np.array([0.5, 0.5])), (Fm, 0.0)):
+        Xg, Yg = pr.X @ A.T + b, pr.Y @ A.T + b
+        pg, st, it, res, _ = o.match(Xg, Yg, k, s, 10, h=0.5, eps=1e-12, maxit=3000)
+        assert st == o.OK
+        assert abs(o.hamiltonian(Xg, pg, k, s) - H) < 1e-9 * H
+        np.testing.assert_allclose(pg, p @ A.T, rtol=0, atol=1e-9)
+
+
+# --------------------------------------------------------------------------- HVP and adjoint
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_hvp_matches_fd_of_gradient(kernel, sigma, dim):
+    """d2H v against central differences of grad H = (-dp, dq) (from the RHS)."""
+    q, p = _cloud(6, dim, seed=31 + dim, spread=0.6, sigma=sigma, kernel=kernel)
+    rng = np.random.default_rng(2)
+    vq, vp = rng.normal(size=q.shape), rng.normal(size=q.shape)
+    hq, hp = o.hvp(q, p, vq, vp, kernel, sigma)
+    h = 1e-6
+    dqa, dpa = o.rhs(q + h * vq, p + h * vp, kernel, sigma)
+    dqb, dpb = o.rhs(q - h * vq, p - h * vp, kernel, sigma)
+    np.testing.assert_allclose(hq, -(dpa - dpb) / (2 * h), rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(hp, (dqa - dqb) / (2 * h), rtol=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adjoint_gradient_matches_central_fd(kernel, sigma, dim):
+    """dE/dp0 for E = 1/2 p0^T G(X) p0 + lam/2 ||Q(1) - Y||^2 (Eq. inexact-E) against
+    central differences with step 1e-4 in FP64."""
+    X, p0 = _cloud(6, dim, seed=41 + dim, spread=0.5, pscale=0.05, sigma=sigma, kernel=kernel)
+    rng = np.random.default_rng(4)
+    Y = X + rng.normal(0, 0.05, size=X.shape)
+    steps, lam = 6, 10.0
+    E, g = o.adjoint(X, p0, Y, kernel, sigma, steps, lam)
+    assert math.isclose(E, o.energy(X, p0, Y, kernel, sigma, steps, lam), rel_tol=1e-13)
+    h = 1e-4
+    fd = np.zeros_like(p0)
+    for i in range(p0.shape[0]):
+        for c in range(dim):
+            e = np.zeros_like(p0)
+            e[i, c] = h
+            fd[i, c] = (o.energy(X, p0 + e, Y, kernel, sigma, steps, lam) -
+                        o.energy(X, p0 - e, Y, kernel, sigma, steps, lam)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+
+
+# --------------------------------------------------------------------------- cell-list predicate
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cell_neighbor_predicate_agrees_with_fp64_distance(dim):
+    rng = np.random.default_rng(9)
+    n = 700 if dim == 2 else 900
+    q = rng.uniform(0, 1, size=(n, dim))
+    sigma = 0.07 if dim == 2 else 0.15
+    cnt, hsh, tot = o.cell_neighbors(q, sigma)
+    d = np.linalg.norm(q[:, None] - q[None], axis=-1)
+    inside = d < sigma * (1 - 1e-5)
+    maybe = d < sigma * (1 + 1e-5)
+    cnt_lo = inside.sum(1)
+    cnt_hi = maybe.sum(1)
+    assert np.all(cnt >= cnt_lo) and np.all(cnt <= cnt_hi)
+    assert tot == int(cnt.sum())
+    # exact agreement away from the boundary band, via the set fingerprint
+    ok = cnt_lo == cnt_hi
+    idx = np.arange(1, n + 1, dtype=np.uint64) * np.uint64(2654435761)
+    fp = np.array([np.sum(idx[inside[i]], dtype=np.uint64) for i in range(n)], dtype=np.uint64)
+    assert np.all(hsh[ok] == fp[ok])
+    assert ok.mean() > 0.99
