@@ -1,0 +1,159 @@
+/*
+ * ep.h -- C ABI of libep.so: GPU (sm_103a) geodesic landmark shooting with the
+ * N-particle Euler-Poincare system of Camassa, Kuang & Lee (arXiv 1510.03816).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Arrays are row-major (n, dim) float64 with dim in {2, 3}: particle i's
+ *    coordinates are a[i*dim + 0 .. i*dim + dim-1].
+ *  - Array pointers may be CUDA device memory or host memory (pageable or
+ *    pinned); the library detects which with cudaPointerGetAttributes and
+ *    stages host arrays through its own device workspace.  The caller owns
+ *    every array; the library never frees or retains them past the call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    stream-ordered and asynchronous when all arrays are device memory, except
+ *    where an entry point says it synchronises.  When any array is host
+ *    memory the call synchronises the stream before returning.
+ *  - The library allocates its workspace itself (cached per device and
+ *    stream, grown on demand, released by ep_release_workspace).
+ *  - Every entry point returns an ep_status and never throws.  On an error the
+ *    outputs are unspecified unless stated; ep_last_error() describes it.
+ *  - Not thread-safe for concurrent calls on the same stream.
+ */
+#ifndef EP_H
+#define EP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EP_OK = 0,
+    EP_EINVAL = 1,        /* bad argument (size, pointer, parameter) */
+    EP_ENOMEM = 2,        /* workspace allocation failed */
+    EP_ECUDA = 3,         /* a CUDA runtime call or kernel failed */
+    EP_ENOTCONVERGED = 4, /* ep_match: iteration cap reached; p0 holds the last iterate */
+    EP_EDIVERGED = 5,     /* ep_match: residual became NaN/Inf; p0 holds the last finite iterate */
+    EP_ETIMEOUT = 6       /* a device-side bounded wait gave up (kernel returned early) */
+} ep_status;
+
+/* Kernels G(r) of the N-particle system (Sec. 3 of the paper).
+ *  EP_GAUSS   G = exp(-r^2 / (2 sigma^2))   smooth kernel of the metric H^inf (Sec. 6)
+ *  EP_TENT    G = max(1 - r/sigma, 0)       compactly supported cone; enables the cell list
+ *  EP_EXPCONE G = exp(-r / sigma)           the paper's "conon" (Eq. nu=3/2, alpha = sigma) */
+typedef enum { EP_GAUSS = 0, EP_TENT = 1, EP_EXPCONE = 2 } ep_kernel;
+
+/* EP_FP64: every operation in FP64 (the plain comparison path).
+ * EP_MIXED: pair terms in FP32, per-particle sums accumulated in FP64, RK4
+ *           step state in FP64, feedback residual and momentum update in FP64. */
+typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
+
+/* EP_AUTO picks the cell list for EP_TENT when it pays off, else all-pairs. */
+typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
+
+typedef struct {
+    int dim;        /* 2 or 3 */
+    int kernel;     /* ep_kernel */
+    double sigma;   /* kernel width, > 0 */
+    int steps;      /* RK4 steps S >= 1 on [0, t1] */
+    double t1;      /* end time; 1.0 for the matching problem (Eq. exact-matching) */
+    int precision;  /* ep_precision */
+    int neigh;      /* ep_neigh */
+} ep_params;
+
+typedef struct {
+    double h;        /* in: gain of M = h I (<= 0: h = 1 / max_i sum_j G_ij); out: gain used */
+    double eps;      /* in: stop when max_i,c |Y - Q(1)| < eps */
+    int maxit;       /* in: maximum number of momentum updates (>= 0) */
+    int iters;       /* out: number of updates performed (shoots = iters + 1) */
+    double resid_inf;/* out: max-norm residual of the last shoot */
+    double H;        /* out: Hamiltonian H(X, p0) of Eq. H for the returned p0 */
+    double* hist;    /* in, optional: maxit + 1 doubles (host or device) that receive the
+                        residual of every shoot; NULL for none */
+} ep_match_info;
+
+/* Right-hand side of the N-particle system (Sec. 3.1, Eq. N-particle):
+ *   dq_i =  sum_j G(|q_i - q_j|) p_j                    (j = i included, G(0) = 1)
+ *   dp_i = -sum_{j != i} (p_i . p_j) G'(r_ij) (q_i - q_j) / r_ij
+ * Tent and expcone take the dp term of a coincident pair (r = 0) as zero; the tent's
+ * dp term vanishes for r >= sigma.  q, p: inputs (n, dim); dq, dp: outputs (n, dim).
+ * n = 0 is a no-op.  Errors: EP_EINVAL for a bad params/n/pointer. */
+ep_status ep_rhs(const ep_params* params, int64_t n, const double* q, const double* p,
+                 double* dq, double* dp, void* stream);
+
+/* Geodesic shoot (Sec. 4, Algorithm 1 step 1): classical RK4 (Note 1 item 5) with
+ * params->steps uniform steps from (q0, p0) at t = 0 to t = params->t1.  Outputs
+ * q1, p1 (n, dim); they may alias q0, p0. */
+ep_status ep_shoot(const ep_params* params, int64_t n, const double* q0, const double* p0,
+                   double* q1, double* p1, void* stream);
+
+/* Feedback-control matching (Sec. 4, Algorithm 1 with the constant gain M = h I of
+ * Sec. 5, applied to the momenta): repeat { Q(1) = shoot(X, p0); r = Y - Q(1);
+ * stop if max|r| < eps; p0 += h r } at most info->maxit updates.  p0: in = initial
+ * guess (zeros for the paper's default, Note 1 item 4), out = last iterate.  The
+ * residual and the update are FP64 in both precisions.  Synchronises the stream
+ * (the stopping test is read on the host each iteration).  Returns EP_OK,
+ * EP_ENOTCONVERGED or EP_EDIVERGED; info is filled in all three cases. */
+ep_status ep_match(const ep_params* params, int64_t n, const double* X, const double* Y,
+                   double* p0, ep_match_info* info, void* stream);
+
+/* Gradient of the inexact-matching energy (Sec. 6, Eq. inexact-E, written with
+ * Eq. E=2H):  E(p0) = 1/2 p0^T G(X) p0 + lambda/2 ||Q(1) - Y||^2  with respect to
+ * p0, by the exact discrete adjoint of the RK4 shoot.  Step states are
+ * checkpointed every ckpt_every steps (>= 1) and recomputed in reverse.
+ * grad_p0: output (n, dim).  energy: output, one double (host or device), may be
+ * NULL. */
+ep_status ep_adjoint(const ep_params* params, int64_t n, const double* X, const double* p0,
+                     const double* Y, double lambda, int ckpt_every, double* grad_p0,
+                     double* energy, void* stream);
+
+/* nprob independent matchings in one persistent launch.  Problem b has
+ * n_b = offsets[b+1] - offsets[b] particles stored at rows offsets[b] .. of X, Y and
+ * p0 (all (offsets[nprob], dim)); params[b] and infos[b] are its parameters and
+ * result (host arrays; infos[b].hist is ignored).  offsets: host array of nprob+1
+ * int64 with offsets[0] = 0, non-decreasing.  All problems must share dim.
+ * Synchronises the stream.  Returns EP_OK when every problem converged, else
+ * the first non-OK status in problem order. */
+ep_status ep_match_batched(const ep_params* params, int nprob, const int64_t* offsets,
+                           const double* X, const double* Y, double* p0, ep_match_info* infos,
+                           void* stream);
+
+/* Discrete Hamiltonian (Sec. 3.1, Eq. H): H = 1/2 sum_i sum_j (p_i . p_j) G(|q_i - q_j|)
+ * (the kinetic energy of Eq. E=2H is 2H).  H_out: one double (host or device). */
+ep_status ep_hamiltonian(const ep_params* params, int64_t n, const double* q, const double* p,
+                         double* H_out, void* stream);
+
+/* Hessian of H applied to v = (vq, vp): (hq, hp) = d2H(q, p) . (vq, vp).  This is the
+ * pair kernel of the adjoint (the transposed stage Jacobian is J^T w = d2H . (-w_p, w_q)).
+ * All arrays (n, dim). */
+ep_status ep_hvp(const ep_params* params, int64_t n, const double* q, const double* p,
+                 const double* vq, const double* vp, double* hq, double* hp, void* stream);
+
+/* Neighbour sets of the cell-list path (EP_TENT only) at positions q (n, dim), for
+ * validation: count[i] = number of accepted j (self included) and
+ * hash[i] = sum over accepted j of (j + 1) * 2654435761 mod 2^64.  The grid and the
+ * FP32 acceptance test are the ones the cell-list RHS uses: cell edge
+ * h = sigma (1 + 2^-8) per axis (wider when more than 2048 (2-D) / 256 (3-D) cells
+ * would be needed), origin min(q) - 2h, local FP32 offsets in units of sigma, and
+ * accept iff fmaf(d0, d0, d1*d1 [+ d2*d2]) < 1.0f.  count, hash: outputs (n) int64
+ * and uint64; total: output, one int64 (host or device), may be NULL. */
+ep_status ep_cell_neighbors(const ep_params* params, int64_t n, const double* q, int64_t* count,
+                            uint64_t* hash, int64_t* total, void* stream);
+
+/* Free the cached device workspaces of every stream (synchronises the device). */
+ep_status ep_release_workspace(void);
+
+/* Message describing the last error on the calling host thread ("" if none). */
+const char* ep_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int ep_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EP_H */

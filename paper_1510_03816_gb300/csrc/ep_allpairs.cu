@@ -1,0 +1,779 @@
+// ep_allpairs.cu -- all-pairs right-hand side of the N-particle system
+// (Sec. 3.1, Eq. N-particle) with the classical RK4 stage (Sec. 4, Note 1
+// item 5) fused into the kernel.
+//
+// Work decomposition (stream-K over the pair matrix).  Particles i are grouped
+// in tiles of 64 (32 lanes x 2 registers).  The pair matrix is the sequence of
+// U = ntiles * n units (tile b, source j), cut into G equal contiguous ranges,
+// one per CTA, G = (SM count) x (resident CTAs per SM).  A CTA's range covers
+// one or a few tile segments [j0, j1).  For each segment the CTA stages the
+// FP32 source data of [j0, j1) in shared memory, its warps split the j range,
+// every lane accumulates its two particles' sums in registers (FP32), the
+// warps' partials are summed in shared memory, and the CTA adds its partial
+// into the FP64 accumulator K of the tile's particles (red.global.add.f64:
+// the per-particle sums are accumulated in FP64).  The last CTA to arrive at
+// a tile (per-tile counter) applies the RK4 stage to the tile's particles:
+// it reads k = K, forms the next stage input, resets K and the counter.
+//
+// Precision modes: EP_MIXED evaluates pair terms in FP32 on scaled
+// coordinates (see ep_common.cuh), keeps the step state x_n in FP64 and the
+// RK4 stage combination in FP32; EP_FP64 does every operation in FP64.
+#include <stdio.h>
+
+#include "ep_allpairs.cuh"
+
+namespace ep {
+
+namespace {
+
+constexpr int kChunk = 2048;  // sources staged per shared-memory fill (mixed)
+constexpr int kChunk64 = 1024;
+
+struct StageArgs {
+    long long U;
+    int n;
+    int G;
+    int mode;
+    int stage;
+    float dt_f;
+    double dt;
+    float s_f;
+    double s;
+    double dp_scale;
+    float dp_scale_f;
+    const double* c0;
+    const float4* S_in;
+    float4* S_out;
+    const float4* Sx;   // step-start stage copy (mixed)
+    float4* Sx_w;       // written at stage 3 (mixed)
+    const double* D_in; // fp64 stage copies
+    double* D_out;
+    double* x;
+    float* acc;
+    double* dacc;
+    double* K;
+    int* counters;
+    double* out_q;
+    double* out_p;
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Kernel value G and momentum weight w of one pair from the scaled squared
+// distance r2 = |d'|^2 (see ep_common.cuh for the scalings).
+template <int KER>
+__device__ __forceinline__ void kfun_f32(float r2, float& G, float& w)
+{
+    if constexpr (KER == EP_GAUSS) {
+        G = ex2_approx(-r2);
+        w = G;
+    } else if constexpr (KER == EP_TENT) {
+        // r2 = 0 (self or coincident pair): rs stays finite and d' = 0, so the
+        // momentum term vanishes (phi = 0 at r = 0) while G(0) = 1.
+        const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
+        const bool in = r2 < 1.0f;
+        G = in ? fmaf(-r2, rs, 1.0f) : 0.0f;
+        w = in ? rs : 0.0f;
+    } else {
+        const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
+        G = ex2_approx(-r2 * rs);
+        w = G * rs;
+    }
+}
+
+// Exact FP64 kernel value and phi = G'(r)/r (unscaled).
+template <int KER>
+__device__ __forceinline__ void kfun_f64(double r2, double sigma, double& G, double& phi)
+{
+    if constexpr (KER == EP_GAUSS) {
+        G = exp(-r2 / (2.0 * sigma * sigma));
+        phi = -G / (sigma * sigma);
+    } else if constexpr (KER == EP_TENT) {
+        const double r = sqrt(r2);
+        const bool in = r < sigma;
+        G = in ? 1.0 - r / sigma : 0.0;
+        phi = (in && r > 0.0) ? -1.0 / (sigma * r) : 0.0;
+    } else {
+        const double r = sqrt(r2);
+        G = exp(-r / sigma);
+        phi = r > 0.0 ? -G / (sigma * r) : 0.0;
+    }
+}
+
+__device__ __forceinline__ int cta_of_unit(long long u, long long U, int G)
+{
+    return (int)(((u + 1) * (long long)G - 1) / U);
+}
+
+__device__ __forceinline__ int tile_contributors(int b, const StageArgs& a)
+{
+    const long long ub = (long long)b * a.n;
+    return cta_of_unit(ub + a.n - 1, a.U, a.G) - cta_of_unit(ub, a.U, a.G) + 1;
+}
+
+// ------------------------------------------------------------------ mixed
+// Epilogue of one particle i in tile order; k = (dq, dp) of the stage input.
+template <int DIM>
+__device__ void epilogue_mixed(const StageArgs& a, int i)
+{
+    constexpr int V = DIM == 2 ? 1 : 2;
+    double kk[kKWidth];
+#pragma unroll
+    for (int t = 0; t < kKWidth; ++t) {
+        kk[t] = __ldcg(a.K + (size_t)i * kKWidth + t);
+        a.K[(size_t)i * kKWidth + t] = 0.0;
+    }
+    // momentum of the stage input (FP32 copy) for the 2-D contraction
+    float pin[3];
+    if constexpr (DIM == 2) {
+        const float4 v = a.S_in[i];
+        pin[0] = v.z;
+        pin[1] = v.w;
+    } else {
+        const float4 v = a.S_in[2 * (size_t)i + 1];
+        pin[0] = v.x;
+        pin[1] = v.y;
+        pin[2] = v.z;
+    }
+    if (a.mode == MODE_RHS) {
+        double kq[DIM], kp[DIM];
+        if constexpr (DIM == 2) {
+            kq[0] = kk[0];
+            kq[1] = kk[1];
+            kp[0] = a.dp_scale * (kk[2] * (double)pin[0] + kk[3] * (double)pin[1]);
+            kp[1] = a.dp_scale * (kk[4] * (double)pin[0] + kk[5] * (double)pin[1]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                kq[c] = kk[c];
+                kp[c] = a.dp_scale * kk[3 + c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            a.out_q[(size_t)i * DIM + c] = kq[c];
+            a.out_p[(size_t)i * DIM + c] = kp[c];
+        }
+        return;
+    }
+    float kq[DIM], kp[DIM];
+    if constexpr (DIM == 2) {
+        kq[0] = (float)kk[0];
+        kq[1] = (float)kk[1];
+        kp[0] = a.dp_scale_f * fmaf((float)kk[2], pin[0], (float)kk[3] * pin[1]);
+        kp[1] = a.dp_scale_f * fmaf((float)kk[4], pin[0], (float)kk[5] * pin[1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            kq[c] = (float)kk[c];
+            kp[c] = a.dp_scale_f * (float)kk[3 + c];
+        }
+    }
+    float* A = a.acc + (size_t)i * 2 * DIM;
+    if (a.stage < 3) {
+        // y_{s+1} = x_n + c_{s+1} dt k_s, c = 1/2, 1/2, 1 (FP32, scaled positions)
+        const float cdt = (a.stage == 2 ? 1.0f : 0.5f) * a.dt_f;
+        const float bw = a.stage == 0 ? 1.0f : 2.0f;
+        float xs[2 * DIM];
+        if constexpr (DIM == 2) {
+            const float4 v = a.Sx[i];
+            xs[0] = v.x; xs[1] = v.y; xs[2] = v.z; xs[3] = v.w;
+        } else {
+            const float4 v0 = a.Sx[2 * (size_t)i], v1 = a.Sx[2 * (size_t)i + 1];
+            xs[0] = v0.x; xs[1] = v0.y; xs[2] = v0.z; xs[3] = v1.x; xs[4] = v1.y; xs[5] = v1.z;
+        }
+        float y[2 * DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            y[c] = fmaf(cdt * a.s_f, kq[c], xs[c]);
+            y[DIM + c] = fmaf(cdt, kp[c], xs[DIM + c]);
+            if (a.stage == 0) {
+                A[c] = kq[c];
+                A[DIM + c] = kp[c];
+            } else {
+                A[c] = fmaf(bw, kq[c], A[c]);
+                A[DIM + c] = fmaf(bw, kp[c], A[DIM + c]);
+            }
+        }
+        if constexpr (DIM == 2) {
+            a.S_out[i] = make_float4(y[0], y[1], y[2], y[3]);
+        } else {
+            a.S_out[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
+            a.S_out[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
+        }
+    } else {
+        // x_{n+1} = x_n + dt/6 (k1 + 2 k2 + 2 k3 + k4): the increment in FP32, the state in FP64
+        const int n = a.n;
+        double* xq = a.x + (size_t)i * DIM;
+        double* xp = a.x + (size_t)n * DIM + (size_t)i * DIM;
+        float y[2 * DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            const double nq = xq[c] + (double)(a.dt_f * (1.0f / 6.0f) * (A[c] + kq[c]));
+            const double np = xp[c] + (double)(a.dt_f * (1.0f / 6.0f) * (A[DIM + c] + kp[c]));
+            xq[c] = nq;
+            xp[c] = np;
+            y[c] = (float)((nq - a.c0[c]) * a.s);
+            y[DIM + c] = (float)np;
+        }
+        if constexpr (DIM == 2) {
+            a.Sx_w[i] = make_float4(y[0], y[1], y[2], y[3]);
+        } else {
+            a.Sx_w[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
+            a.Sx_w[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
+        }
+    }
+}
+
+template <int DIM, int KER, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
+{
+    constexpr int W = THREADS / 32;
+    constexpr int V = DIM == 2 ? 1 : 2;  // float4 per particle
+    extern __shared__ float4 smem[];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n = a.n;
+    long long u0 = (long long)blockIdx.x * a.U / a.G;
+    const long long u1 = (long long)(blockIdx.x + 1) * a.U / a.G;
+
+    while (u0 < u1) {
+        const int b = (int)(u0 / n);
+        const int j0 = (int)(u0 - (long long)b * n);
+        const int j1 = (int)min((long long)n, (long long)j0 + (u1 - u0));
+
+        // the two particles of this lane (zeros beyond n contribute nothing used)
+        float qi[2][DIM], pi[2][DIM];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int i = b * kTileI + lane + 32 * r;
+            if (i < n) {
+                if constexpr (DIM == 2) {
+                    const float4 v = a.S_in[i];
+                    qi[r][0] = v.x; qi[r][1] = v.y; pi[r][0] = v.z; pi[r][1] = v.w;
+                } else {
+                    const float4 v0 = a.S_in[2 * (size_t)i], v1 = a.S_in[2 * (size_t)i + 1];
+                    qi[r][0] = v0.x; qi[r][1] = v0.y; qi[r][2] = v0.z;
+                    pi[r][0] = v1.x; pi[r][1] = v1.y; pi[r][2] = v1.z;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) { qi[r][c] = 0.0f; pi[r][c] = 0.0f; }
+            }
+        }
+        float acc[2][kKWidth];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int t = 0; t < kKWidth; ++t) acc[r][t] = 0.0f;
+
+        for (int cj = j0; cj < j1; cj += kChunk) {
+            const int L = min(kChunk, j1 - cj);
+            __syncthreads();
+            for (int t = threadIdx.x; t < L * V; t += THREADS) smem[t] = a.S_in[(size_t)cj * V + t];
+            __syncthreads();
+            const int ja = warp * L / W, jb = (warp + 1) * L / W;
+#pragma unroll 4
+            for (int j = ja; j < jb; ++j) {
+                if constexpr (DIM == 2) {
+                    const float4 v = smem[j];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const float dx = qi[r][0] - v.x, dy = qi[r][1] - v.y;
+                        const float r2 = fmaf(dx, dx, dy * dy);
+                        float G, w;
+                        kfun_f32<KER>(r2, G, w);
+                        acc[r][0] = fmaf(G, v.z, acc[r][0]);
+                        acc[r][1] = fmaf(G, v.w, acc[r][1]);
+                        const float tx = w * dx, ty = w * dy;
+                        acc[r][2] = fmaf(tx, v.z, acc[r][2]);
+                        acc[r][3] = fmaf(tx, v.w, acc[r][3]);
+                        acc[r][4] = fmaf(ty, v.z, acc[r][4]);
+                        acc[r][5] = fmaf(ty, v.w, acc[r][5]);
+                    }
+                } else {
+                    const float4 v0 = smem[2 * j], v1 = smem[2 * j + 1];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const float dx = qi[r][0] - v0.x, dy = qi[r][1] - v0.y, dz = qi[r][2] - v0.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        float G, w;
+                        kfun_f32<KER>(r2, G, w);
+                        acc[r][0] = fmaf(G, v1.x, acc[r][0]);
+                        acc[r][1] = fmaf(G, v1.y, acc[r][1]);
+                        acc[r][2] = fmaf(G, v1.z, acc[r][2]);
+                        const float pp = fmaf(pi[r][0], v1.x, fmaf(pi[r][1], v1.y, pi[r][2] * v1.z));
+                        const float c = w * pp;
+                        acc[r][3] = fmaf(c, dx, acc[r][3]);
+                        acc[r][4] = fmaf(c, dy, acc[r][4]);
+                        acc[r][5] = fmaf(c, dz, acc[r][5]);
+                    }
+                }
+            }
+        }
+
+        // warps' partials -> shared memory [W][6][64] -> FP64 accumulator
+        __syncthreads();
+        float* red = reinterpret_cast<float*>(smem);
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int t = 0; t < kKWidth; ++t) red[(warp * kKWidth + t) * kTileI + lane + 32 * r] = acc[r][t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < kKWidth * kTileI; t += THREADS) {
+            const int k = t / kTileI, il = t % kTileI;
+            float s = 0.0f;
+#pragma unroll 8
+            for (int w2 = 0; w2 < W; ++w2) s += red[(w2 * kKWidth + k) * kTileI + il];
+            const int i = b * kTileI + il;
+            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, (double)s);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int prev = atomicAdd(a.counters + b, 1);
+            s_last = (prev == tile_contributors(b, a) - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (threadIdx.x < kTileI) {
+                const int i = b * kTileI + threadIdx.x;
+                if (i < n) epilogue_mixed<DIM>(a, i);
+            }
+            if (threadIdx.x == 0) a.counters[b] = 0;
+        }
+        u0 += (j1 - j0);
+    }
+}
+
+// ------------------------------------------------------------------ fp64
+template <int DIM>
+__device__ void epilogue_fp64(const StageArgs& a, int i, double sigma_unused)
+{
+    (void)sigma_unused;
+    double kq[DIM], kp[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        kq[c] = __ldcg(a.K + (size_t)i * kKWidth + c);
+        kp[c] = __ldcg(a.K + (size_t)i * kKWidth + 3 + c);
+        a.K[(size_t)i * kKWidth + c] = 0.0;
+        a.K[(size_t)i * kKWidth + 3 + c] = 0.0;
+    }
+    if (a.mode == MODE_RHS) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            a.out_q[(size_t)i * DIM + c] = kq[c];
+            a.out_p[(size_t)i * DIM + c] = kp[c];
+        }
+        return;
+    }
+    const int n = a.n;
+    double* xq = a.x + (size_t)i * DIM;
+    double* xp = a.x + (size_t)n * DIM + (size_t)i * DIM;
+    double* A = a.dacc + (size_t)i * 2 * DIM;
+    if (a.stage < 3) {
+        const double cdt = (a.stage == 2 ? 1.0 : 0.5) * a.dt;
+        const double bw = a.stage == 0 ? 1.0 : 2.0;
+        double* out = a.D_out + (size_t)i * 2 * DIM;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            out[c] = xq[c] + cdt * kq[c];
+            out[DIM + c] = xp[c] + cdt * kp[c];
+            A[c] = (a.stage == 0 ? 0.0 : A[c]) + bw * kq[c];
+            A[DIM + c] = (a.stage == 0 ? 0.0 : A[DIM + c]) + bw * kp[c];
+        }
+    } else {
+        double* out = a.D_out + (size_t)i * 2 * DIM;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            const double nq = xq[c] + a.dt / 6.0 * (A[c] + kq[c]);
+            const double np = xp[c] + a.dt / 6.0 * (A[DIM + c] + kp[c]);
+            xq[c] = nq;
+            xp[c] = np;
+            out[c] = nq;
+            out[DIM + c] = np;
+        }
+    }
+}
+
+template <int DIM, int KER, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_stage_fp64(StageArgs a, double sigma)
+{
+    constexpr int W = THREADS / 32;
+    constexpr int S = 2 * DIM;  // doubles per particle in the stage copy
+    extern __shared__ double dsm[];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n = a.n;
+    long long u0 = (long long)blockIdx.x * a.U / a.G;
+    const long long u1 = (long long)(blockIdx.x + 1) * a.U / a.G;
+    while (u0 < u1) {
+        const int b = (int)(u0 / n);
+        const int j0 = (int)(u0 - (long long)b * n);
+        const int j1 = (int)min((long long)n, (long long)j0 + (u1 - u0));
+        double qi[2][DIM], pi[2][DIM];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int i = b * kTileI + lane + 32 * r;
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                qi[r][c] = i < n ? a.D_in[(size_t)i * S + c] : 0.0;
+                pi[r][c] = i < n ? a.D_in[(size_t)i * S + DIM + c] : 0.0;
+            }
+        }
+        double acc[2][2 * DIM];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int t = 0; t < 2 * DIM; ++t) acc[r][t] = 0.0;
+        for (int cj = j0; cj < j1; cj += kChunk64) {
+            const int L = min(kChunk64, j1 - cj);
+            __syncthreads();
+            for (int t = threadIdx.x; t < L * S; t += THREADS) dsm[t] = a.D_in[(size_t)cj * S + t];
+            __syncthreads();
+            const int ja = warp * L / W, jb = (warp + 1) * L / W;
+            for (int j = ja; j < jb; ++j) {
+                const double* v = dsm + (size_t)j * S;
+                const int jg = cj + j;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    double d[DIM], r2 = 0.0, pp = 0.0;
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) {
+                        d[c] = qi[r][c] - v[c];
+                        r2 += d[c] * d[c];
+                        pp += pi[r][c] * v[DIM + c];
+                    }
+                    double G, phi;
+                    kfun_f64<KER>(r2, sigma, G, phi);
+                    const int i = b * kTileI + lane + 32 * r;
+                    const double wgt = (jg == i) ? 0.0 : -pp * phi;
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) {
+                        acc[r][c] += G * v[DIM + c];
+                        acc[r][DIM + c] += wgt * d[c];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        double* red = dsm;  // [W][2*DIM][64]
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int t = 0; t < 2 * DIM; ++t) red[(warp * 2 * DIM + t) * kTileI + lane + 32 * r] = acc[r][t];
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * DIM * kTileI; t += THREADS) {
+            const int k = t / kTileI, il = t % kTileI;
+            double s = 0.0;
+            for (int w2 = 0; w2 < W; ++w2) s += red[(w2 * 2 * DIM + k) * kTileI + il];
+            const int i = b * kTileI + il;
+            const int slot = k < DIM ? k : 3 + (k - DIM);
+            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + slot, s);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int prev = atomicAdd(a.counters + b, 1);
+            s_last = (prev == tile_contributors(b, a) - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (threadIdx.x < kTileI) {
+                const int i = b * kTileI + threadIdx.x;
+                if (i < n) epilogue_fp64<DIM>(a, i, sigma);
+            }
+            if (threadIdx.x == 0) a.counters[b] = 0;
+        }
+        u0 += (j1 - j0);
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+// c0 = centre of the bounding box of q (one CTA).
+__global__ void k_bbox_center(const double* __restrict__ q, int n, int dim, double* c0)
+{
+    __shared__ double smin[3][32], smax[3][32];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int c = 0; c < dim; ++c) {
+            const double v = q[(size_t)i * dim + c];
+            mn[c] = fmin(mn[c], v);
+            mx[c] = fmax(mx[c], v);
+        }
+    for (int c = 0; c < dim; ++c)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[c] = fmin(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+            mx[c] = fmax(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+        }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int c = 0; c < dim; ++c) { smin[c][w] = mn[c]; smax[c][w] = mx[c]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int c = 0; c < 3; ++c) {
+            double a = INFINITY, b2 = -INFINITY;
+            if (c < dim)
+                for (int k = 0; k < nw; ++k) { a = fmin(a, smin[c][k]); b2 = fmax(b2, smax[c][k]); }
+            c0[c] = (c < dim && n > 0) ? 0.5 * (a + b2) : 0.0;
+        }
+    }
+}
+
+// x = [q | p] and the step-start stage copy.
+__global__ void k_load_state(const double* __restrict__ q, const double* __restrict__ p, int n, int dim,
+                             double* __restrict__ x, const double* __restrict__ c0, double s,
+                             float4* __restrict__ Sx, double* __restrict__ Dx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double qq[3] = {0, 0, 0}, pp[3] = {0, 0, 0};
+    for (int c = 0; c < dim; ++c) {
+        qq[c] = q[(size_t)i * dim + c];
+        pp[c] = p[(size_t)i * dim + c];
+        x[(size_t)i * dim + c] = qq[c];
+        x[(size_t)n * dim + (size_t)i * dim + c] = pp[c];
+    }
+    if (Sx) {
+        float y[3];
+        for (int c = 0; c < 3; ++c) y[c] = c < dim ? (float)((qq[c] - c0[c]) * s) : 0.0f;
+        if (dim == 2) {
+            Sx[i] = make_float4(y[0], y[1], (float)pp[0], (float)pp[1]);
+        } else {
+            Sx[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
+            Sx[2 * (size_t)i + 1] = make_float4((float)pp[0], (float)pp[1], (float)pp[2], 0.0f);
+        }
+    }
+    if (Dx) {
+        for (int c = 0; c < dim; ++c) {
+            Dx[(size_t)i * 2 * dim + c] = qq[c];
+            Dx[(size_t)i * 2 * dim + dim + c] = pp[c];
+        }
+    }
+}
+
+template <int DIM, int KER, int THREADS>
+ep_status launch_mixed(const StageArgs& a, cudaStream_t st)
+{
+    constexpr int W = THREADS / 32;
+    constexpr int V = DIM == 2 ? 1 : 2;
+    const size_t smem = std::max((size_t)kChunk * V * sizeof(float4), (size_t)W * kKWidth * kTileI * sizeof(float));
+    static bool attr = false;
+    if (!attr) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(k_stage_mixed<DIM, KER, THREADS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_stage_mixed<DIM, KER, THREADS><<<a.G, THREADS, smem, st>>>(a);
+    return EP_OK;
+}
+
+template <int DIM, int KER>
+ep_status launch_fp64(const StageArgs& a, double sigma, cudaStream_t st)
+{
+    constexpr int THREADS = 256;
+    constexpr int W = THREADS / 32;
+    const size_t smem = std::max((size_t)kChunk64 * 2 * DIM * sizeof(double),
+                                 (size_t)W * 2 * DIM * kTileI * sizeof(double));
+    static bool attr = false;
+    if (!attr) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(k_stage_fp64<DIM, KER, THREADS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_stage_fp64<DIM, KER, THREADS><<<a.G, THREADS, smem, st>>>(a, sigma);
+    return EP_OK;
+}
+
+ep_status launch_stage(const ep_params& P, const StageArgs& a, int threads, cudaStream_t st)
+{
+#define EP_MIXED_CASE(D, K)                                                       \
+    if (P.dim == D && P.kernel == K) {                                            \
+        if (threads == 1024) return launch_mixed<D, K, 1024>(a, st);              \
+        if (threads == 512) return launch_mixed<D, K, 512>(a, st);                \
+        return launch_mixed<D, K, 256>(a, st);                                    \
+    }
+#define EP_FP64_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) return launch_fp64<D, K>(a, P.sigma, st);
+    if (P.precision == EP_MIXED) {
+        EP_MIXED_CASE(2, EP_GAUSS) EP_MIXED_CASE(2, EP_TENT) EP_MIXED_CASE(2, EP_EXPCONE)
+        EP_MIXED_CASE(3, EP_GAUSS) EP_MIXED_CASE(3, EP_TENT) EP_MIXED_CASE(3, EP_EXPCONE)
+    } else {
+        EP_FP64_CASE(2, EP_GAUSS) EP_FP64_CASE(2, EP_TENT) EP_FP64_CASE(2, EP_EXPCONE)
+        EP_FP64_CASE(3, EP_GAUSS) EP_FP64_CASE(3, EP_TENT) EP_FP64_CASE(3, EP_EXPCONE)
+    }
+#undef EP_MIXED_CASE
+#undef EP_FP64_CASE
+    set_error("no all-pairs kernel for dim=%d kernel=%d precision=%d", P.dim, P.kernel, P.precision);
+    return EP_EINVAL;
+}
+
+StageArgs base_args(const ep_params& P, const AllPairsBufs& b, const APConfig& cfg)
+{
+    StageArgs a{};
+    const int ntiles = (b.n + kTileI - 1) / kTileI;
+    a.n = b.n;
+    a.U = (long long)ntiles * b.n;
+    a.G = (int)std::min<long long>(cfg.ctas, a.U);
+    const KernelScale ks = kernel_scale(P.kernel, P.sigma);
+    a.s = ks.s;
+    a.s_f = (float)ks.s;
+    a.dp_scale = ks.dp_scale;
+    a.dp_scale_f = (float)ks.dp_scale;
+    a.c0 = b.c0;
+    a.x = b.x;
+    a.acc = b.acc;
+    a.dacc = b.dacc;
+    a.K = b.K;
+    a.counters = b.counters;
+    return a;
+}
+
+}  // namespace
+
+size_t allpairs_bytes(int n, int dim, int prec)
+{
+    Sizer z;
+    const int ntiles = (n + kTileI - 1) / kTileI;
+    z.add(sizeof(double) * 2 * dim * (size_t)n);   // x
+    z.add(sizeof(double) * kKWidth * (size_t)n);   // K
+    z.add(sizeof(int) * (size_t)ntiles);           // counters
+    z.add(sizeof(double) * 4);                     // c0
+    if (prec == EP_MIXED) {
+        const int V = dim == 2 ? 1 : 2;
+        for (int k = 0; k < 3; ++k) z.add(sizeof(float4) * V * (size_t)n);
+        z.add(sizeof(float) * 2 * dim * (size_t)n);
+    } else {
+        for (int k = 0; k < 3; ++k) z.add(sizeof(double) * 2 * dim * (size_t)n);
+        z.add(sizeof(double) * 2 * dim * (size_t)n);
+    }
+    return z.total;
+}
+
+ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b)
+{
+    const int ntiles = (n + kTileI - 1) / kTileI;
+    b->n = n;
+    b->dim = dim;
+    b->prec = prec;
+    b->x = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
+    b->K = (double*)ar->carve(sizeof(double) * kKWidth * (size_t)n);
+    b->counters = (int*)ar->carve(sizeof(int) * (size_t)ntiles);
+    b->c0 = (double*)ar->carve(sizeof(double) * 4);
+    if (prec == EP_MIXED) {
+        const int V = dim == 2 ? 1 : 2;
+        b->Sx = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
+        b->Sa = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
+        b->Sb = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
+        b->acc = (float*)ar->carve(sizeof(float) * 2 * dim * (size_t)n);
+        if (!b->acc) return set_error("workspace too small"), EP_ENOMEM;
+    } else {
+        b->Dx = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
+        b->Da = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
+        b->Db = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
+        b->dacc = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
+        if (!b->dacc) return set_error("workspace too small"), EP_ENOMEM;
+    }
+    if (!b->c0) return set_error("workspace too small"), EP_ENOMEM;
+    return EP_OK;
+}
+
+APConfig allpairs_config(int n, int dim, int prec, int kernel)
+{
+    (void)dim;
+    (void)kernel;
+    APConfig c;
+    DeviceInfo di{};
+    if (device_info(&di) != EP_OK) di.sm_count = 1;
+    if (prec == EP_MIXED) {
+        c.threads = 1024;
+        c.ctas = di.sm_count;
+    } else {
+        c.threads = 256;
+        c.ctas = di.sm_count * 4;
+    }
+    // keep at least ~256 units (pairs per lane-pair) per CTA for tiny problems
+    const long long ntiles = (n + kTileI - 1) / kTileI;
+    const long long U = ntiles * (long long)n;
+    const long long maxc = std::max<long long>(1, U / 256);
+    c.ctas = (int)std::max<long long>(1, std::min<long long>(c.ctas, maxc));
+    return c;
+}
+
+ep_status allpairs_load(const ep_params& P, const AllPairsBufs& b, const double* q, const double* p,
+                        cudaStream_t st)
+{
+    const int n = b.n;
+    const int ntiles = (n + kTileI - 1) / kTileI;
+    EP_TRY_CUDA(cudaMemsetAsync(b.K, 0, sizeof(double) * kKWidth * (size_t)n, st));
+    EP_TRY_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)ntiles, st));
+    k_bbox_center<<<1, 1024, 0, st>>>(q, n, P.dim, b.c0);
+    const KernelScale ks = kernel_scale(P.kernel, P.sigma);
+    if (n > 0)
+        k_load_state<<<(n + 255) / 256, 256, 0, st>>>(q, p, n, P.dim, b.x, b.c0, ks.s, b.Sx, b.Dx);
+    EP_TRY_CUDA(cudaGetLastError());
+    return EP_OK;
+}
+
+ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, double* dp, cudaStream_t st)
+{
+    if (b.n == 0) return EP_OK;
+    const APConfig cfg = allpairs_config(b.n, P.dim, P.precision, P.kernel);
+    StageArgs a = base_args(P, b, cfg);
+    a.mode = MODE_RHS;
+    a.stage = 0;
+    a.S_in = b.Sx;
+    a.D_in = b.Dx;
+    a.out_q = dq;
+    a.out_p = dp;
+    EP_TRY(launch_stage(P, a, cfg.threads, st));
+    EP_TRY_CUDA(cudaGetLastError());
+    return EP_OK;
+}
+
+ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt, cudaStream_t st)
+{
+    if (b.n == 0 || steps == 0) return EP_OK;
+    const APConfig cfg = allpairs_config(b.n, P.dim, P.precision, P.kernel);
+    StageArgs a = base_args(P, b, cfg);
+    a.mode = MODE_RK4;
+    a.dt = dt;
+    a.dt_f = (float)dt;
+    a.Sx = b.Sx;
+    a.Sx_w = b.Sx;
+    for (int s = 0; s < steps; ++s) {
+        for (int stage = 0; stage < 4; ++stage) {
+            a.stage = stage;
+            // stage inputs: Sx -> Sa -> Sb -> Sa, stage 3 writes the next Sx
+            if (P.precision == EP_MIXED) {
+                a.S_in = stage == 0 ? b.Sx : (stage == 2 ? b.Sb : b.Sa);
+                a.S_out = stage == 1 ? b.Sb : b.Sa;
+            } else {
+                a.D_in = stage == 0 ? b.Dx : (stage == 2 ? b.Db : b.Da);
+                a.D_out = stage == 3 ? b.Dx : (stage == 1 ? b.Db : b.Da);
+            }
+            EP_TRY(launch_stage(P, a, cfg.threads, st));
+        }
+    }
+    EP_TRY_CUDA(cudaGetLastError());
+    return EP_OK;
+}
+
+}  // namespace ep

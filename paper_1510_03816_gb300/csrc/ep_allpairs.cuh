@@ -1,0 +1,50 @@
+// ep_allpairs.cuh -- all-pairs RHS / fused RK4 stage kernels (declarations).
+#pragma once
+
+#include "ep_common.cuh"
+
+namespace ep {
+
+enum StageMode { MODE_RK4 = 0, MODE_RHS = 1 };
+
+// Device buffers of one all-pairs problem of n particles.  Mixed precision uses
+// the float4 stage copies; FP64 mode uses the double stage copies.
+struct AllPairsBufs {
+    int n = 0, dim = 2, prec = EP_MIXED;
+    double* x = nullptr;     // FP64 step state [q (n*dim) | p (n*dim)]
+    double* K = nullptr;     // FP64 k accumulator, n * kKWidth, zero between launches
+    int* counters = nullptr; // per-tile arrival counters, zero between launches
+    double* c0 = nullptr;    // origin of the scaled coordinates (3 doubles)
+    // mixed
+    float4* Sx = nullptr;    // step-start stage copy (stage-0 input)
+    float4* Sa = nullptr;    // stage copies (ping-pong)
+    float4* Sb = nullptr;
+    float* acc = nullptr;    // FP32 RK4 accumulator, n * 2 * dim
+    // fp64
+    double* Dx = nullptr;
+    double* Da = nullptr;
+    double* Db = nullptr;
+    double* dacc = nullptr;  // FP64 RK4 accumulator
+};
+
+size_t allpairs_bytes(int n, int dim, int prec);
+ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b);
+
+// Launch configuration (CTA count, threads) chosen by the tuner.
+struct APConfig {
+    int threads = 1024;
+    int ctas = 0;
+};
+APConfig allpairs_config(int n, int dim, int prec, int kernel);
+
+// x <- (q, p); stage copy Sx/Dx <- x; K, counters zeroed; c0 = bbox centre of q.
+ep_status allpairs_load(const ep_params& P, const AllPairsBufs& b, const double* q,
+                        const double* p, cudaStream_t st);
+// One RHS evaluation at the state in x; writes dq, dp (device, n*dim each).
+ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, double* dp,
+                       cudaStream_t st);
+// steps RK4 steps of size dt from the state in x (x updated in place).
+ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt,
+                         cudaStream_t st);
+
+}  // namespace ep

@@ -1,0 +1,36 @@
+// ep_features.cuh -- entry points and buffers of the cell-list, adjoint and
+// batched paths (declarations shared with ep_api.cu).
+#pragma once
+
+#include "ep_common.cuh"
+
+namespace ep {
+
+// ---------------------------------------------------------------- cell list (tent kernel)
+struct CellBufs {
+    int n = 0, dim = 2, prec = EP_MIXED;
+    double* x = nullptr;  // FP64 step state [q (n*dim) | p (n*dim)]
+    void* impl = nullptr; // remaining buffers, owned by ep_celllist.cu
+    char* raw = nullptr;
+    size_t raw_bytes = 0;
+};
+size_t cell_bytes(int n, int dim, int prec);
+ep_status cell_carve(Arena* ar, int n, int dim, int prec, CellBufs* b);
+ep_status cell_load(const ep_params& P, const CellBufs& b, const double* q, const double* p, cudaStream_t st);
+ep_status cell_rhs(const ep_params& P, const CellBufs& b, double* dq, double* dp, cudaStream_t st);
+ep_status cell_steps(const ep_params& P, const CellBufs& b, int steps, double dt, cudaStream_t st);
+
+bool use_celllist(const ep_params& P, int64_t n);
+
+// ---------------------------------------------------------------- entry points
+ep_status cell_neighbors_entry(const ep_params* params, int64_t n, const double* q, int64_t* count,
+                               uint64_t* hash, int64_t* total, void* stream);
+ep_status hvp_entry(const ep_params* params, int64_t n, const double* q, const double* p, const double* vq,
+                    const double* vp, double* hq, double* hp, void* stream);
+ep_status adjoint_entry(const ep_params* params, int64_t n, const double* X, const double* p0,
+                        const double* Y, double lambda, int ckpt_every, double* grad_p0, double* energy,
+                        void* stream);
+ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offsets, const double* X,
+                        const double* Y, double* p0, ep_match_info* infos, void* stream);
+
+}  // namespace ep
