@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 landmark-shooting library (libep.so).
+
+One step = one complete feedback-control matching (Algorithm 1 of arXiv
+1510.03816, gain M = h I on the momenta, p0 = 0, eps = 1e-6, at most 200
+updates) of the N = 4096 planar Fourier-curve workload (Gaussian kernel
+sigma = 0.1, RK4 with 100 steps, mixed precision: FP32 pair terms, FP64
+per-particle sums, FP64 residual and momentum update), through ep_match.
+
+Reported (one JSON line on rank 0):
+  value        pair interactions per second over the whole job (every (i, j)
+               term the method evaluates: N^2 per RHS, 400 RHS per shoot, plus
+               the default-gain and final-Hamiltonian evaluations), device-
+               resident inputs, summed over ranks
+  e2e          the same metric through ep_match with pinned host buffers
+               (host<->device copies inside the timed region)
+  roofline     the dominant kernel (the fused all-pairs RK4 stage) against the
+               FP32 ALU peak derived from unit counts and the maximum clock
+  cpu_baseline the FP64 CPU oracle on the host cores, on a bounded sample
+  shoots_per_s, endpoint_err_vs_fp64, fp64_shoots_per_s: the shoot metric
+               against the plain FP64 GPU shoot from the same momenta
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+the same workload and metric, each step a bounded sample.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload
+(replicas only: the path has no data exchange), time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "pair interactions/s in EP RHS; shoots/s to 1e-6 endpoint err vs plain FP64"
+UNIT = "pair interactions/s"
+FP32_LANES_PER_SM = 128
+FLOPS_PER_PAIR_2D_GAUSS = 19  # algorithmic flops of one (i, j) term of Eq. N-particle, exp counted as 1
+WORKLOAD = ("fourier_curve_warp: N=4096 2-D landmarks on a random Fourier curve -> sine warp; "
+            "Gaussian sigma=0.1; RK4 100 steps on [0,1]; Algorithm 1 from p0=0, eps=1e-6 (max-norm), maxit=200; "
+            "default gain h = 1/max_i sum_j G_ij")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--maxit", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run warmup + steps shoots of the workload (for ncu captures); no JSON line")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local, dist
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def pairs_of(n: int, steps: int, shoots: int) -> int:
+    # 4 RHS per RK4 step per shoot, + the default-gain RHS + the final-H RHS
+    return n * n * (4 * steps * shoots + 2)
+
+
+def run_gb300(args):
+    import torch
+
+    from paper_1510_03816_gb300 import build, ep, workloads
+
+    world, rank, local, dist = dist_setup(args)
+    build.build()
+    ep.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    pr = workloads.fourier_curve_warp()
+    n, S = pr.n, pr.steps
+    X = torch.tensor(pr.X, device=dev)
+    Y = torch.tensor(pr.Y, device=dev)
+    prm = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=S, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+
+    def step():
+        return ep.match(X, Y, prm, h=0.0, eps=pr.eps, maxit=args.maxit)
+
+    if args.profile:
+        p0 = 0.002 * (Y - X)
+        for _ in range(args.warmup + args.steps):
+            ep.shoot(X, p0, prm)
+        torch.cuda.synchronize()
+        return
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[local] if vis else local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ep.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    shoots = 0
+    last = None
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        last = step()
+        ev[k][1].record(stream)
+        shoots += last.iters + 1
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = ep.launch_count() - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    clk = clocks.stop()
+    local_pairs = n * n * (4 * S * shoots + 2 * args.steps)
+    t_max = ms
+    total_pairs = local_pairs
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([float(local_pairs)], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_pairs = float(c.item())
+    value = total_pairs / (t_max / 1e3)
+
+    # ---- dominant kernel: the fused all-pairs stage, timed on the launch stream
+    p_fin = last.p0
+    R = 3
+    for _ in range(1):
+        ep.shoot(X, p_fin, prm)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(R):
+        q1m, _p1m = ep.shoot(X, p_fin, prm)
+    b.record(stream)
+    torch.cuda.synchronize()
+    shoot_ms = a.elapsed_time(b) / R
+    launch_ms = shoot_ms / (4 * S)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    achieved = FLOPS_PER_PAIR_2D_GAUSS * n * n / (launch_ms / 1e3) / 1e12
+
+    # ---- plain FP64 GPU shoot from the same momenta (the comparison point of the shoot metric)
+    prm64 = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=S, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    a.record(stream)
+    q1d, _ = ep.shoot(X, p_fin, prm64)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = a.elapsed_time(b)
+    err = float((q1m - q1d).abs().max().item())
+
+    # ---- end to end through the public API with pinned host buffers
+    Xh = torch.tensor(pr.X).pin_memory()
+    Yh = torch.tensor(pr.Y).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_shoots = 0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r = ep.match(Xh, Yh, prm, h=0.0, eps=pr.eps, maxit=args.maxit)
+        e2e_shoots += r.iters + 1
+    e2e_s = time.perf_counter() - t0
+    e2e_pairs = n * n * (4 * S * e2e_shoots + 2 * e2e_steps)
+    h2d = 3 * n * 2 * 8  # X, Y, p0 (zeros) per step
+    d2h = n * 2 * 8 + 16 * (e2e_shoots // e2e_steps) + 16  # p0, per-shoot residual, gain and H
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "rk4_steps": S, "precision": "FP32 pair terms, FP64 sums/state/residual",
+                   "shoots_per_step": shoots / args.steps, "l2": "256 MiB buffer written between steps (untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "shoots_per_s": world * shoots / (t_max / 1e3),
+        "endpoint_err_vs_fp64": err,
+        "fp64_shoots_per_s": 1e3 / fp64_ms,
+        "roofline": {"bound": "alu", "kernel": "k_stage_mixed<2,GAUSS,1024> (fused all-pairs RK4 stage)",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": None, "launch_us": launch_ms * 1e3,
+                     "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)",
+                     "flops_per_pair": FLOPS_PER_PAIR_2D_GAUSS},
+        "e2e": {"value": e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(pr, p_fin.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(pr, p0, budget_s: float = 15.0) -> dict:
+    """The FP64 oracle (as it stands) on the host cores: an RK4 shoot of the same
+    workload with as many steps as fit in about budget_s seconds."""
+    from oracle import oracle
+
+    oracle.build()
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.rhs(pr.X, p0, pr.kernel, pr.sigma)
+    t_rhs = time.perf_counter() - t0
+    steps = max(1, int(budget_s / (4 * t_rhs)))
+    t0 = time.perf_counter()
+    oracle.shoot(pr.X, p0, pr.kernel, pr.sigma, steps)
+    dt = time.perf_counter() - t0
+    pairs = pr.n * pr.n * 4 * steps
+    return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle RK4 shoot of the N={pr.n} workload, {steps} steps ({4 * steps} RHS, "
+                      f"{pairs:.3e} pair interactions) in {dt:.1f} s on {cores} threads"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step an RK4 shoot sample."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle
+
+    from paper_1510_03816_gb300 import workloads
+
+    oracle.build()
+    pr = workloads.fourier_curve_warp()
+    p0 = 0.002 * (pr.Y - pr.X)
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.rhs(pr.X, p0, pr.kernel, pr.sigma)
+    t_rhs = time.perf_counter() - t0
+    steps_per_sample = max(1, int(2.0 / (4 * t_rhs)))
+    for _ in range(args.warmup):
+        oracle.shoot(pr.X, p0, pr.kernel, pr.sigma, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.shoot(pr.X, p0, pr.kernel, pr.sigma, steps_per_sample)
+    dt = time.perf_counter() - t0
+    pairs = pr.n * pr.n * 4 * steps_per_sample * args.steps
+    value = pairs / dt
+    sample = (f"per step: FP64 oracle RK4 shoot of the N={pr.n} workload with {steps_per_sample} RK4 steps "
+              f"({4 * steps_per_sample} RHS) on {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": pr.n, "rk4_steps_per_sample": steps_per_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

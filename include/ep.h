@@ -149,6 +149,10 @@ ep_status ep_release_workspace(void);
 /* Message describing the last error on the calling host thread ("" if none). */
 const char* ep_last_error(void);
 
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices and streams); a monotone counter for instrumentation. */
+int64_t ep_launch_count(void);
+
 /* Library version: major * 10000 + minor * 100 + patch. */
 int ep_version(void);
 

@@ -20,6 +20,8 @@
 // RK4 stage combination in FP32; EP_FP64 does every operation in FP64.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "ep_allpairs.cuh"
 
 namespace ep {
@@ -581,6 +583,7 @@ ep_status launch_mixed(const StageArgs& a, cudaStream_t st)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    count_launch();
     k_stage_mixed<DIM, KER, THREADS><<<a.G, THREADS, smem, st>>>(a);
     return EP_OK;
 }
@@ -598,6 +601,7 @@ ep_status launch_fp64(const StageArgs& a, double sigma, cudaStream_t st)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
+    count_launch();
     k_stage_fp64<DIM, KER, THREADS><<<a.G, THREADS, smem, st>>>(a, sigma);
     return EP_OK;
 }
@@ -697,12 +701,12 @@ ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b)
 
 APConfig allpairs_config(int n, int dim, int prec, int kernel)
 {
-    (void)dim;
     (void)kernel;
     APConfig c;
     DeviceInfo di{};
     if (device_info(&di) != EP_OK) di.sm_count = 1;
     if (prec == EP_MIXED) {
+        // one CTA per SM
         c.threads = 1024;
         c.ctas = di.sm_count;
     } else {
@@ -724,10 +728,13 @@ ep_status allpairs_load(const ep_params& P, const AllPairsBufs& b, const double*
     const int ntiles = (n + kTileI - 1) / kTileI;
     EP_TRY_CUDA(cudaMemsetAsync(b.K, 0, sizeof(double) * kKWidth * (size_t)n, st));
     EP_TRY_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)ntiles, st));
+    count_launch();
     k_bbox_center<<<1, 1024, 0, st>>>(q, n, P.dim, b.c0);
     const KernelScale ks = kernel_scale(P.kernel, P.sigma);
-    if (n > 0)
+    if (n > 0) {
+        count_launch();
         k_load_state<<<(n + 255) / 256, 256, 0, st>>>(q, p, n, P.dim, b.x, b.c0, ks.s, b.Sx, b.Dx);
+    }
     EP_TRY_CUDA(cudaGetLastError());
     return EP_OK;
 }

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -16,6 +17,11 @@
 #include "ep_features.cuh"
 
 namespace ep {
+
+// ------------------------------------------------------------------ launch counter
+static std::atomic<long long> g_launches{0};
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ errors
 static thread_local char g_err[512] = "";
@@ -313,9 +319,11 @@ static double* forward_state(const Forward& f) { return f.cells ? f.cl.x : f.ap.
 static ep_status default_gain(const ep_params& P, const Forward& f, int64_t n, const double* X, double* unit,
                               double* dq, double* dp, double* scal, cudaStream_t st, double* h_out)
 {
+    count_launch();
     k_fill_unit_x<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(unit, (int)n, P.dim);
     EP_TRY(forward_load(P, f, X, unit, st));
     EP_TRY(forward_rhs(P, f, dq, dp, st));
+    count_launch();
     k_max_first<<<1, 1024, 0, st>>>(dq, (int)n, P.dim, scal);
     double mx = 0.0;
     EP_TRY_CUDA(cudaMemcpyAsync(&mx, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -333,6 +341,8 @@ static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 extern "C" {
 
 int ep_version(void) { return 10000; }
+
+int64_t ep_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
 const char* ep_last_error(void) { return g_err; }
 
@@ -444,6 +454,7 @@ ep_status ep_hamiltonian(const ep_params* params, int64_t n, const double* q, co
     double* scal = (double*)ar->carve(64);
     EP_TRY(forward_load(P, f, sq.dev, sp.dev, st));
     EP_TRY(forward_rhs(P, f, dq, dp, st));
+    count_launch();
     k_half_dot<<<1, 1024, 0, st>>>(sp.dev, dq, m, hout_dev ? H_out : scal);
     if (!hout_dev) {
         EP_TRY_CUDA(cudaMemcpyAsync(H_out, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -506,7 +517,8 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     for (;;) {
         EP_TRY(forward_load(P, f, sX.dev, sp.dev, st));
         EP_TRY(forward_steps(P, f, P.steps, dt, st));
-        k_max_abs_diff<<<1, 1024, 0, st>>>(sY.dev, Q1, m, scal);
+        count_launch();
+    k_max_abs_diff<<<1, 1024, 0, st>>>(sY.dev, Q1, m, scal);
         EP_TRY_CUDA(cudaMemcpyAsync(host_res, scal, sizeof host_res, cudaMemcpyDeviceToHost, st));
         EP_TRY_CUDA(cudaStreamSynchronize(st));
         const bool finite = host_res[1] == 0.0;
@@ -518,7 +530,8 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         if (!finite) { status = EP_EDIVERGED; break; }
         if (res < info->eps) { status = EP_OK; break; }
         if (k == info->maxit) { status = EP_ENOTCONVERGED; break; }
-        k_momentum_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(sp.dev, sY.dev, Q1, m, h);
+        count_launch();
+    k_momentum_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(sp.dev, sY.dev, Q1, m, h);
         ++k;
     }
     info->iters = k;
@@ -526,6 +539,7 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     // H(X, p0) of the returned momenta (Eq. H)
     EP_TRY(forward_load(P, f, sX.dev, sp.dev, st));
     EP_TRY(forward_rhs(P, f, t0, t1, st));
+    count_launch();
     k_half_dot<<<1, 1024, 0, st>>>(sp.dev, t0, m, scal);
     EP_TRY_CUDA(cudaMemcpyAsync(&info->H, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (sp.host) EP_TRY_CUDA(cudaMemcpyAsync(p0, sp.dev, sizeof(double) * m, cudaMemcpyDeviceToHost, st));

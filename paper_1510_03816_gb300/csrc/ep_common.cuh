@@ -47,6 +47,10 @@ inline KernelScale kernel_scale(int kernel, double sigma)
     return k;
 }
 
+// ---------------------------------------------------------------- launch counter
+// Incremented once per kernel launch (exported as ep_launch_count).
+void count_launch(int k = 1);
+
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
 ep_status cuda_fail(cudaError_t e, const char* what);

@@ -32,7 +32,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libep.so")
 
 # Every symbol include/ep.h declares (checked by the ABI test).
 EXPORTS = ("ep_rhs", "ep_shoot", "ep_match", "ep_adjoint", "ep_match_batched", "ep_hamiltonian",
-           "ep_hvp", "ep_cell_neighbors", "ep_release_workspace", "ep_last_error", "ep_version")
+           "ep_hvp", "ep_cell_neighbors", "ep_release_workspace", "ep_last_error", "ep_version",
+           "ep_launch_count")
 
 
 class EPError(RuntimeError):
@@ -97,6 +98,8 @@ def load():
     lib.ep_last_error.argtypes = []
     lib.ep_version.restype = ctypes.c_int
     lib.ep_version.argtypes = []
+    lib.ep_launch_count.restype = ctypes.c_int64
+    lib.ep_launch_count.argtypes = []
     _lib = lib
     return lib
 
@@ -107,6 +110,11 @@ def last_error() -> str:
 
 def version() -> int:
     return int(load().ep_version())
+
+
+def launch_count() -> int:
+    """Kernels libep.so has launched in this process (ep_launch_count)."""
+    return int(load().ep_launch_count())
 
 
 def release_workspace() -> None:
@@ -142,8 +150,10 @@ def _prep(a, name: str):
 
 def _empty_like(a, shape=None, dtype=None):
     if _is_torch(a):
+        pin = (not a.is_cuda) and a.is_pinned()
         return torch.empty(shape if shape is not None else a.shape,
-                           dtype=dtype if dtype is not None else torch.float64, device=a.device)
+                           dtype=dtype if dtype is not None else torch.float64, device=a.device,
+                           pin_memory=pin)
     return np.empty(shape if shape is not None else a.shape, dtype=dtype if dtype is not None else np.float64)
 
 
@@ -214,8 +224,12 @@ def match(X, Y, prm: Params, h: float = 0.0, eps: float = 1e-6, maxit: int = 200
         else:
             p[...] = 0.0
     else:
-        p, _ = _prep(p0, "p0")
-        p = p.clone() if _is_torch(p) else p.copy()
+        src, _ = _prep(p0, "p0")
+        p = _empty_like(src)
+        if _is_torch(p):
+            p.copy_(src)
+        else:
+            p[...] = src
     hbuf = np.full(maxit + 1, np.nan) if hist else None
     info = MatchInfo(float(h), float(eps), int(maxit), 0, 0.0, 0.0, hbuf.ctypes.data if hist else None)
     st = load().ep_match(ctypes.byref(_with_dim(prm, dim)), n, xp, yp, _ptr(p), ctypes.byref(info),
