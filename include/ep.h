@@ -143,6 +143,27 @@ ep_status ep_hvp(const ep_params* params, int64_t n, const double* q, const doub
 ep_status ep_cell_neighbors(const ep_params* params, int64_t n, const double* q, int64_t* count,
                             uint64_t* hash, int64_t* total, void* stream);
 
+/* ep_rhs for callers that may not allocate device memory during the call.  The
+ * paper has no counterpart: this is a library-interface variant of ep_rhs.
+ * Some callers cannot call cudaMalloc at that point, for example a real-time or
+ * callback context where cudaMalloc's implicit synchronisation is not allowed, or
+ * a host framework whose memory pool owns the device.  This call takes all its
+ * scratch from a fixed array compiled into the library (about 1.25 MiB on every
+ * device that loads libep.so, held until the process exits) and never allocates.
+ * Limits and rules:
+ *  - n <= EP_NOALLOC_MAX_N; larger n returns EP_EINVAL.
+ *  - all-pairs path only (params->neigh == EP_CELLLIST returns EP_EINVAL);
+ *  - q, p, dq, dp must be device memory (host arrays return EP_EINVAL);
+ *  - the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call shares the one array; calls whose GPU work overlaps (for
+ *    example on two unordered streams) race and give wrong results.
+ * Results are those of ep_rhs (same kernels). */
+#define EP_NOALLOC_MAX_N 8192
+ep_status ep_rhs_noalloc(const ep_params* params, int64_t n, const double* q, const double* p,
+                         double* dq, double* dp, void* stream);
+
 /* Free the cached device workspaces of every stream (synchronises the device). */
 ep_status ep_release_workspace(void);
 

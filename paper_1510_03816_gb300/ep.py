@@ -33,7 +33,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libep.so")
 # Every symbol include/ep.h declares (checked by the ABI test).
 EXPORTS = ("ep_rhs", "ep_shoot", "ep_match", "ep_adjoint", "ep_match_batched", "ep_hamiltonian",
            "ep_hvp", "ep_cell_neighbors", "ep_release_workspace", "ep_last_error", "ep_version",
-           "ep_launch_count")
+           "ep_launch_count", "ep_rhs_noalloc")
 
 
 class EPError(RuntimeError):
@@ -81,6 +81,7 @@ def load():
     I64, VP, D = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
     sig = {
         "ep_rhs": [P, I64, VP, VP, VP, VP, VP],
+        "ep_rhs_noalloc": [P, I64, VP, VP, VP, VP, VP],
         "ep_shoot": [P, I64, VP, VP, VP, VP, VP],
         "ep_match": [P, I64, VP, VP, VP, ctypes.POINTER(MatchInfo), VP],
         "ep_adjoint": [P, I64, VP, VP, VP, D, ctypes.c_int, VP, VP, VP],
@@ -187,6 +188,19 @@ def rhs(q, p, prm: Params):
     n, dim = _shape(q)
     dq, dp = _empty_like(q), _empty_like(q)
     _check(load().ep_rhs(ctypes.byref(_with_dim(prm, dim)), n, qp, pp, _ptr(dq), _ptr(dp), _stream_for(q)))
+    return dq, dp
+
+
+def rhs_noalloc(q, p, prm: Params, dq=None, dp=None):
+    """ep_rhs_noalloc: ep_rhs without any allocation inside the library (device arrays,
+    n <= 8192).  Pass preallocated dq, dp to keep the call free of allocations here too."""
+    q, qp = _prep(q, "q")
+    p, pp = _prep(p, "p")
+    n, dim = _shape(q)
+    dq = _empty_like(q) if dq is None else dq
+    dp = _empty_like(q) if dp is None else dp
+    _check(load().ep_rhs_noalloc(ctypes.byref(_with_dim(prm, dim)), n, qp, pp, _ptr(dq), _ptr(dp),
+                                 _stream_for(q)))
     return dq, dp
 
 
