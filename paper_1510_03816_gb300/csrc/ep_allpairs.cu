@@ -783,4 +783,40 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
     return EP_OK;
 }
 
+ep_status allpairs_steps_rec(const ep_params& P, const AllPairsBufs& b, int steps, double dt, float4* rec,
+                             double* drec, cudaStream_t st)
+{
+    if (b.n == 0 || steps == 0) return EP_OK;
+    const APConfig cfg = allpairs_config(b.n, P.dim, P.precision, P.kernel);
+    StageArgs a = base_args(P, b, cfg);
+    a.mode = MODE_RK4;
+    a.dt = dt;
+    a.dt_f = (float)dt;
+    const size_t V = P.dim == 2 ? 1 : 2;
+    const size_t cm = V * (size_t)b.n;               // float4 per stage copy
+    const size_t cd = 2 * (size_t)P.dim * b.n;       // doubles per stage copy
+    if (P.precision == EP_MIXED)
+        EP_TRY_CUDA(cudaMemcpyAsync(rec, b.Sx, sizeof(float4) * cm, cudaMemcpyDeviceToDevice, st));
+    else
+        EP_TRY_CUDA(cudaMemcpyAsync(drec, b.Dx, sizeof(double) * cd, cudaMemcpyDeviceToDevice, st));
+    for (int k = 0; k < steps; ++k) {
+        for (int stage = 0; stage < 4; ++stage) {
+            a.stage = stage;
+            const size_t in = 4 * (size_t)k + stage;
+            if (P.precision == EP_MIXED) {
+                a.Sx = rec + 4 * (size_t)k * cm;
+                a.Sx_w = rec + 4 * (size_t)(k + 1) * cm;
+                a.S_in = rec + in * cm;
+                a.S_out = rec + (in + 1) * cm;
+            } else {
+                a.D_in = drec + in * cd;
+                a.D_out = drec + (in + 1) * cd;
+            }
+            EP_TRY(launch_stage(P, a, cfg.threads, st));
+        }
+    }
+    EP_TRY_CUDA(cudaGetLastError());
+    return EP_OK;
+}
+
 }  // namespace ep

@@ -47,4 +47,11 @@ ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, do
 ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt,
                          cudaStream_t st);
 
+// As allpairs_steps, recording every stage input: stage copy 4k + s (s = 0..3) of
+// rec (mixed; float4 x (dim == 2 ? 1 : 2) per particle, scaled positions) or drec
+// (FP64; 2*dim doubles per particle) holds the input of stage s of step k, and
+// copy 4*steps the final state.  rec / drec hold 4*steps + 1 stage copies.
+ep_status allpairs_steps_rec(const ep_params& P, const AllPairsBufs& b, int steps, double dt, float4* rec,
+                             double* drec, cudaStream_t st);
+
 }  // namespace ep

@@ -16,8 +16,6 @@ ep_status cell_load(const ep_params&, const CellBufs&, const double*, const doub
 ep_status cell_rhs(const ep_params&, const CellBufs&, double*, double*, cudaStream_t) { return pending("the cell list"); }
 ep_status cell_steps(const ep_params&, const CellBufs&, int, double, cudaStream_t) { return pending("the cell list"); }
 ep_status cell_neighbors_entry(const ep_params*, int64_t, const double*, int64_t*, uint64_t*, int64_t*, void*) { return pending("ep_cell_neighbors"); }
-ep_status hvp_entry(const ep_params*, int64_t, const double*, const double*, const double*, const double*, double*, double*, void*) { return pending("ep_hvp"); }
-ep_status adjoint_entry(const ep_params*, int64_t, const double*, const double*, const double*, double, int, double*, double*, void*) { return pending("ep_adjoint"); }
 ep_status batched_entry(const ep_params*, int, const int64_t*, const double*, const double*, double*, ep_match_info*, void*) { return pending("ep_match_batched"); }
 
 }  // namespace ep
