@@ -545,3 +545,94 @@ long orc_cell_neighbors(int dim, double sigma, long n, const double* q, long* ou
     free(off);
     return total;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Row-sampled variants, for checks at sizes where the full double loop is   */
+/* too slow: the same sums for the listed particles i only (all j).          */
+/* ------------------------------------------------------------------------ */
+void orc_rhs_rows(int dim, int kernel, double sigma, long n, const double* q, const double* p,
+                  const long* rows, long nrows, double* dq, double* dp)
+{
+    long r;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (r = 0; r < nrows; ++r) {
+        const long i = rows[r];
+        double sq[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
+        const double* qi = q + i * dim;
+        const double* pi = p + i * dim;
+        for (long j = 0; j < n; ++j) {
+            const double* qj = q + j * dim;
+            const double* pj = p + j * dim;
+            double rr = dist(dim, qi, qj);
+            double g = orc_G(kernel, sigma, rr);
+            for (int c = 0; c < dim; ++c) sq[c] += g * pj[c];
+            if (j != i) {
+                double w = dot(dim, pi, pj) * orc_phi(kernel, sigma, rr);
+                for (int c = 0; c < dim; ++c) sp[c] -= w * (qi[c] - qj[c]);
+            }
+        }
+        for (int c = 0; c < dim; ++c) {
+            dq[r * dim + c] = sq[c];
+            dp[r * dim + c] = sp[c];
+        }
+    }
+}
+
+void orc_cell_neighbors_rows(int dim, double sigma, long n, const double* q, const long* rows, long nrows,
+                             long* out_count, unsigned long long* out_hash)
+{
+    double lo[3] = {0, 0, 0}, hc[3] = {1, 1, 1};
+    long nc[3] = {1, 1, 1};
+    orc_cell_grid(dim, sigma, n, q, lo, hc, nc);
+    long* cell = (long*)malloc(sizeof(long) * (size_t)(n * dim + 1));
+    float* off = (float*)malloc(sizeof(float) * (size_t)(n * dim + 1));
+    float e[3];
+    double inv_sigma = 1.0 / sigma;
+    for (int c = 0; c < dim; ++c) e[c] = (float)(hc[c] * inv_sigma);
+    for (long i = 0; i < n; ++i)
+        for (int c = 0; c < dim; ++c) {
+            double t = q[i * dim + c] - lo[c];
+            double inv_h = 1.0 / hc[c];
+            long k = (long)floor(t * inv_h);
+            if (k < 0) k = 0;
+            if (k > nc[c] - 1) k = nc[c] - 1;
+            cell[i * dim + c] = k;
+            off[i * dim + c] = (float)((t - (double)k * hc[c]) * inv_sigma);
+        }
+    long r;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (r = 0; r < nrows; ++r) {
+        const long i = rows[r];
+        long cnt = 0;
+        unsigned long long hsum = 0ULL;
+        for (long j = 0; j < n; ++j) {
+            int adjacent = 1;
+            float d[3] = {0.f, 0.f, 0.f};
+            for (int c = 0; c < dim; ++c) {
+                long dc = cell[i * dim + c] - cell[j * dim + c];
+                if (dc < -1 || dc > 1) { adjacent = 0; break; }
+                float diff = off[i * dim + c] - off[j * dim + c];
+                float shift = (float)dc * e[c];
+                d[c] = diff + shift;
+            }
+            if (!adjacent) continue;
+            float r2;
+            if (dim == 2) {
+                float t1 = d[1] * d[1];
+                r2 = fmaf(d[0], d[0], t1);
+            } else {
+                float t2 = d[2] * d[2];
+                float t1 = fmaf(d[1], d[1], t2);
+                r2 = fmaf(d[0], d[0], t1);
+            }
+            if (r2 < 1.0f) {
+                ++cnt;
+                hsum += (unsigned long long)(j + 1) * 2654435761ULL;
+            }
+        }
+        out_count[r] = cnt;
+        out_hash[r] = hsum;
+    }
+    free(cell);
+    free(off);
+}

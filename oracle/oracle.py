@@ -82,6 +82,10 @@ def _load():
         lib.orc_cell_grid.argtypes = [i, d, l, p, p, p, p]
         lib.orc_cell_neighbors.restype = l
         lib.orc_cell_neighbors.argtypes = [i, d, l, p, p, p]
+        lib.orc_rhs_rows.restype = None
+        lib.orc_rhs_rows.argtypes = [i, i, d, l, p, p, p, l, p, p]
+        lib.orc_cell_neighbors_rows.restype = None
+        lib.orc_cell_neighbors_rows.argtypes = [i, d, l, p, p, l, p, p]
         lib.orc_set_threads.restype = None
         lib.orc_set_threads.argtypes = [i]
         lib.orc_max_threads.restype = i
@@ -235,3 +239,28 @@ def cell_neighbors(q, sigma: float):
     tot = _load().orc_cell_neighbors(dim, sigma, n, _ptr(q), cnt.ctypes.data_as(ctypes.c_void_p),
                                      hsh.ctypes.data_as(ctypes.c_void_p))
     return cnt, hsh, int(tot)
+
+
+def rhs_rows(q, p, rows, kernel: int, sigma: float):
+    """Eq. N-particle for the particles in ``rows`` only (sums over all j)."""
+    q = _arr(q)
+    dim = q.shape[1]
+    p = _arr(p, dim)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    dq = np.empty((rows.size, dim))
+    dp = np.empty((rows.size, dim))
+    _load().orc_rhs_rows(dim, kernel, sigma, q.shape[0], _ptr(q), _ptr(p), rows.ctypes.data_as(ctypes.c_void_p),
+                         rows.size, _ptr(dq), _ptr(dp))
+    return dq, dp
+
+
+def cell_neighbors_rows(q, rows, sigma: float):
+    """Brute-force neighbour sets of the cell-list predicate for the particles in ``rows``."""
+    q = _arr(q)
+    n, dim = q.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cnt = np.zeros(rows.size, dtype=np.int64)
+    hsh = np.zeros(rows.size, dtype=np.uint64)
+    _load().orc_cell_neighbors_rows(dim, sigma, n, _ptr(q), rows.ctypes.data_as(ctypes.c_void_p), rows.size,
+                                    cnt.ctypes.data_as(ctypes.c_void_p), hsh.ctypes.data_as(ctypes.c_void_p))
+    return cnt, hsh

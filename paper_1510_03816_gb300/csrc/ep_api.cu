@@ -272,7 +272,8 @@ bool use_celllist(const ep_params& P, int64_t n)
     if (P.kernel != EP_TENT) return false;
     if (P.neigh == EP_CELLLIST) return true;
     if (P.neigh == EP_ALLPAIRS) return false;
-    return n >= 16384;
+    // EP_AUTO: the cell list (2-D, mixed precision) for large tent problems
+    return P.dim == 2 && P.precision == EP_MIXED && n >= 16384;
 }
 
 // Problem state of one forward pass, whichever neighbour path it uses.
@@ -295,7 +296,7 @@ static ep_status forward_carve(Arena* ar, const ep_params& P, int64_t n, Forward
     return allpairs_carve(ar, (int)n, P.dim, P.precision, &f->ap);
 }
 
-static ep_status forward_load(const ep_params& P, const Forward& f, const double* q, const double* p,
+static ep_status forward_load(const ep_params& P, Forward& f, const double* q, const double* p,
                               cudaStream_t st)
 {
     return f.cells ? cell_load(P, f.cl, q, p, st) : allpairs_load(P, f.ap, q, p, st);
@@ -316,7 +317,7 @@ static double* forward_state(const Forward& f) { return f.cells ? f.cl.x : f.ap.
 // Default gain h = 1 / max_i sum_j G(|X_i - X_j|) (Gershgorin bound on the largest
 // eigenvalue of G(X); all three kernels are non-negative so |G| = G).  Computed with
 // the right-hand side at unit momenta (1, 0[, 0]): dq_i,x = sum_j G_ij.
-static ep_status default_gain(const ep_params& P, const Forward& f, int64_t n, const double* X, double* unit,
+static ep_status default_gain(const ep_params& P, Forward& f, int64_t n, const double* X, double* unit,
                               double* dq, double* dp, double* scal, cudaStream_t st, double* h_out)
 {
     count_launch();

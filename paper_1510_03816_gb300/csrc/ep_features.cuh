@@ -10,13 +10,12 @@ namespace ep {
 struct CellBufs {
     int n = 0, dim = 2, prec = EP_MIXED;
     double* x = nullptr;  // FP64 step state [q (n*dim) | p (n*dim)]
-    void* impl = nullptr; // remaining buffers, owned by ep_celllist.cu
-    char* raw = nullptr;
-    size_t raw_bytes = 0;
+    // device pointers and the grid of the current call, owned by ep_celllist.cu
+    alignas(16) char host[1024];
 };
 size_t cell_bytes(int n, int dim, int prec);
 ep_status cell_carve(Arena* ar, int n, int dim, int prec, CellBufs* b);
-ep_status cell_load(const ep_params& P, const CellBufs& b, const double* q, const double* p, cudaStream_t st);
+ep_status cell_load(const ep_params& P, CellBufs& b, const double* q, const double* p, cudaStream_t st);
 ep_status cell_rhs(const ep_params& P, const CellBufs& b, double* dq, double* dp, cudaStream_t st);
 ep_status cell_steps(const ep_params& P, const CellBufs& b, int steps, double dt, cudaStream_t st);
 

@@ -1,0 +1,131 @@
+"""GPU cell list (tent kernel, 2-D): neighbour sets bit-exact against the oracle's
+brute force of the same predicate, and RHS / shoot / match parity with the FP64
+oracle (mixed precision: RHS <= 1e-5, endpoints <= 1e-3 because of the tent's
+jump at r = sigma), through the C ABI.  At the full 512 x 512 jittered-grid size
+the oracle checks a sample of rows."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as o  # noqa: E402
+from paper_1510_03816_gb300 import ep, workloads as w  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_03816_gb300 import build
+
+    build.build()
+    o.build()
+    ep.load()
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def cuda(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def grid_problem(side, seed_stream=3):
+    pr = w.jittered_grid(side=side, stream=seed_stream)
+    p = 0.01 * (pr.Y - pr.X)
+    return pr, p
+
+
+def boundary_rows(q, sigma, rows=None, band=1e-4):
+    """Particles with a neighbour within band*sigma of distance sigma (the tent's dp
+    weight jumps there, so FP32 and FP64 may legitimately disagree)."""
+    idx = np.arange(q.shape[0]) if rows is None else rows
+    out = np.zeros(idx.size, dtype=bool)
+    for k, i in enumerate(idx):
+        d = np.linalg.norm(q - q[i], axis=1)
+        out[k] = np.any(np.abs(d - sigma) < band * sigma)
+    return out
+
+
+@pytest.mark.parametrize("side,seed", [(24, 1), (64, 2)])
+def test_neighbor_sets_bit_exact(side, seed):
+    pr, _ = grid_problem(side, seed)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, precision=ep.MIXED, neigh=ep.CELLLIST)
+    cnt, hsh, tot = ep.cell_neighbors(cuda(pr.X), prm)
+    rc, rh, rt = o.cell_neighbors(pr.X, pr.sigma)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), rc)
+    np.testing.assert_array_equal(hsh.cpu().numpy().view(np.uint64), rh)
+    assert tot == rt
+
+
+def test_neighbor_sets_random_cloud_and_clamped_outliers():
+    rng = np.random.default_rng(4)
+    q = rng.uniform(0, 1, size=(3000, 2))
+    q[:5] += 3.0  # far outliers stretch the grid: many empty cells
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=0.03, neigh=ep.CELLLIST)
+    cnt, hsh, tot = ep.cell_neighbors(q, prm)  # host arrays
+    rc, rh, rt = o.cell_neighbors(q, 0.03)
+    np.testing.assert_array_equal(cnt, rc)
+    np.testing.assert_array_equal(hsh, rh)
+
+
+def test_neighbor_sets_full_size_sampled_rows():
+    pr = w.jittered_grid()
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, neigh=ep.CELLLIST)
+    cnt, hsh, tot = ep.cell_neighbors(cuda(pr.X), prm)
+    rows = np.random.default_rng(0).choice(pr.n, 2000, replace=False)
+    rc, rh = o.cell_neighbors_rows(pr.X, rows, pr.sigma)
+    np.testing.assert_array_equal(cnt.cpu().numpy()[rows], rc)
+    np.testing.assert_array_equal(hsh.cpu().numpy().view(np.uint64)[rows], rh)
+    assert 25 < tot / pr.n < 40  # about 32 neighbours + self per particle
+
+
+def test_rhs_parity_and_against_all_pairs():
+    pr, p = grid_problem(64)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, precision=ep.MIXED, neigh=ep.CELLLIST)
+    dq, dp = ep.rhs(cuda(pr.X), cuda(p), prm)
+    rq, rp = o.rhs(pr.X, p, ep.TENT, pr.sigma)
+    keep = ~boundary_rows(pr.X, pr.sigma)
+    assert rel(dq, rq) < 1e-5
+    assert rel(dp.cpu().numpy()[keep], rp[keep]) < 1e-5
+    prm_ap = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    aq, apv = ep.rhs(cuda(pr.X), cuda(p), prm_ap)
+    assert rel(dq, aq.cpu().numpy()) < 1e-5
+
+
+def test_rhs_full_size_sampled_rows():
+    pr = w.jittered_grid()
+    p = 0.01 * (pr.Y - pr.X)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, neigh=ep.CELLLIST)
+    dq, dp = ep.rhs(cuda(pr.X), cuda(p), prm)
+    rows = np.random.default_rng(1).choice(pr.n, 1500, replace=False)
+    rq, rp = o.rhs_rows(pr.X, p, rows, ep.TENT, pr.sigma)
+    keep = ~boundary_rows(pr.X, pr.sigma, rows)
+    assert rel(dq.cpu().numpy()[rows], rq) < 1e-5
+    assert rel(dp.cpu().numpy()[rows][keep], rp[keep]) < 1e-5
+
+
+def test_shoot_and_match_parity():
+    pr, p = grid_problem(40)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, steps=6, precision=ep.MIXED, neigh=ep.CELLLIST)
+    q1, p1 = ep.shoot(cuda(pr.X), cuda(p), prm)
+    rq, rp = o.shoot(pr.X, p, ep.TENT, pr.sigma, 6)
+    assert rel(q1, rq) < 1e-3 and rel(p1, rp) < 1e-3
+    assert np.abs(q1.cpu().numpy() - rq).max() < 1e-6
+    r = ep.match(cuda(pr.X), cuda(pr.Y), prm, h=0.02, eps=1e-9, maxit=4)
+    pm, st, it, res, hist = o.match(pr.X, pr.Y, ep.TENT, pr.sigma, 6, h=0.02, eps=1e-9, maxit=4)
+    assert r.iters == it
+    assert rel(r.p0, pm) < 1e-3
+    np.testing.assert_allclose(r.hist, hist, rtol=1e-3)
+
+
+def test_cell_list_is_deterministic():
+    pr, p = grid_problem(48)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, steps=3, neigh=ep.CELLLIST)
+    a = ep.shoot(cuda(pr.X), cuda(p), prm)[0]
+    b = ep.shoot(cuda(pr.X), cuda(p), prm)[0]
+    assert torch.equal(a, b)

@@ -352,3 +352,20 @@ def test_cell_neighbor_predicate_agrees_with_fp64_distance(dim):
     fp = np.array([np.sum(idx[inside[i]], dtype=np.uint64) for i in range(n)], dtype=np.uint64)
     assert np.all(hsh[ok] == fp[ok])
     assert ok.mean() > 0.99
+
+
+def test_row_sampled_variants_equal_the_full_sums():
+    """The row-sampled RHS and neighbour sets are the full functions restricted to rows."""
+    rng = np.random.default_rng(12)
+    q = rng.uniform(0, 1, size=(500, 2))
+    p = rng.normal(0, 0.1, size=(500, 2))
+    rows = np.array([0, 17, 250, 499])
+    for k, s in KERNELS:
+        dq, dp = o.rhs(q, p, k, s)
+        rq, rp = o.rhs_rows(q, p, rows, k, s)
+        np.testing.assert_array_equal(rq, dq[rows])
+        np.testing.assert_array_equal(rp, dp[rows])
+    cnt, hsh, _ = o.cell_neighbors(q, 0.06)
+    rc, rh = o.cell_neighbors_rows(q, rows, 0.06)
+    np.testing.assert_array_equal(rc, cnt[rows])
+    np.testing.assert_array_equal(rh, hsh[rows])
