@@ -1,0 +1,541 @@
+// ep_batched.cu -- many independent matchings (Algorithm 1 of the paper, gain
+// M = h I on the momenta) in one persistent launch.
+//
+// Work distribution.  Problems are ordered by decreasing cost (n^2, longest
+// processing time first) and handed out through two global counters.  The
+// launch is a grid of thread-block clusters of kCluster CTAs, sized to what can
+// be resident at once, so no CTA ever waits for one that is not running:
+//   - "team" problems (n >= team_min): all CTAs of a cluster solve one problem
+//     together.  CTA r owns the particle slice [r n / C, (r+1) n / C); every
+//     CTA keeps the whole problem's FP32 stage records in its shared memory, and
+//     after each RK4 stage each CTA writes its slice's new records into the
+//     shared memory of every CTA of the cluster (distributed shared memory),
+//     separated by hardware cluster barriers;
+//   - "solo" problems: each CTA solves one problem alone, independently of the
+//     others in its cluster.
+// Each solve runs the whole feedback loop on the GPU: the shoot (RK4 stages
+// with the pair sums over all sources in shared memory, FP32 pair terms,
+// per-particle sums folded into FP64 every kFold sources), the FP64 max-norm
+// residual, the FP64 momentum update, and finally H(X, p0) (Eq. H).
+//
+// Scaled coordinates as in the all-pairs path: q' = s (q - c0), c0 the centre of
+// the bounding box of X, s and the momentum factor dp_scale from the kernel.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "ep_features.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ep {
+
+namespace {
+
+constexpr int kCluster = 8;
+constexpr int kThreads = 1024;
+constexpr int kMaxN = 8192;          // particles per problem (shared-memory records)
+constexpr int kMaxPerThread = 2;     // particles i per thread and CTA slice
+constexpr int kFold = 512;           // FP32 partial sums folded into FP64 every kFold sources
+
+struct BProb {
+    long long off;   // first row in X, Y, p0
+    int n;
+    int kernel;
+    int steps;
+    int maxit;
+    double sigma;
+    double t1;
+    double h;
+    double eps;
+    double s;        // coordinate scale
+    double dp_scale;
+};
+
+struct BOut {
+    int iters;
+    int status;      // ep_status of this problem
+    double resid;
+    double H;
+    double h;
+};
+
+struct BArgs {
+    const BProb* probs;
+    BOut* outs;
+    const int* order;   // team problems first, each group by decreasing cost
+    int nteam;
+    int nprob;
+    int* ctr;           // [0] team counter, [1] solo counter
+    const double* X;
+    const double* Y;
+    double* p0;
+    double* xs;         // FP64 step state, 4 doubles per particle: (qx, qy, px, py)
+    float* acc;         // FP32 RK4 accumulator, 4 floats per particle
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void kfun(int ker, float r2, float& G, float& w)
+{
+    if (ker == EP_GAUSS) {
+        G = ex2_approx(-r2);
+        w = G;
+    } else if (ker == EP_TENT) {
+        const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
+        const bool in = r2 < 1.0f;
+        G = in ? fmaf(-r2, rs, 1.0f) : 0.0f;
+        w = in ? rs : 0.0f;
+    } else {
+        const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
+        G = ex2_approx(-r2 * rs);
+        w = G * rs;
+    }
+}
+
+// Team context: the CTAs that solve one problem together.
+struct Team {
+    int rank, size;
+    bool cluster;
+};
+
+__device__ __forceinline__ void team_sync(const Team& t)
+{
+    if (t.cluster) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// Sum (or max) of one double per CTA over the team; every thread gets the result.
+__device__ double team_reduce(const Team& t, double v, bool take_max, double* s_red, double* s_slot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = take_max ? fmax(v, u) : v + u;
+    }
+    if (lane == 0) s_red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = take_max ? -INFINITY : 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) a = take_max ? fmax(a, s_red[k]) : a + s_red[k];
+        *s_slot = a;
+    }
+    team_sync(t);
+    double r = take_max ? -INFINITY : 0.0;
+    if (t.cluster) {
+        cg::cluster_group cl = cg::this_cluster();
+        for (int k = 0; k < t.size; ++k) {
+            const double u = *cl.map_shared_rank(s_slot, k);
+            r = take_max ? fmax(r, u) : r + u;
+        }
+    } else {
+        r = *s_slot;
+    }
+    team_sync(t);
+    return r;
+}
+
+// Pair sums over all n sources in shared memory for the thread's particles
+// (slice [lo, hi), stride kThreads); k = (dq, dp) per particle.
+__device__ void pair_sums(const float4* rec, int n, int lo, int hi, int ker, float dp_scale, float (&kq)[kMaxPerThread][2],
+                          float (&kp)[kMaxPerThread][2])
+{
+#pragma unroll
+    for (int r = 0; r < kMaxPerThread; ++r) {
+        const int i = lo + threadIdx.x + r * kThreads;
+        kq[r][0] = kq[r][1] = kp[r][0] = kp[r][1] = 0.f;
+        if (i >= hi) continue;
+        const float4 ri = rec[i];
+        double aq0 = 0, aq1 = 0, ap0 = 0, ap1 = 0;
+        for (int j0 = 0; j0 < n; j0 += kFold) {
+            const int j1 = min(n, j0 + kFold);
+            float q0 = 0.f, q1 = 0.f, p0 = 0.f, p1 = 0.f;
+            for (int j = j0; j < j1; ++j) {
+                const float4 rj = rec[j];
+                const float dx = ri.x - rj.x, dy = ri.y - rj.y;
+                const float r2 = fmaf(dx, dx, dy * dy);
+                float G, w;
+                kfun(ker, r2, G, w);
+                q0 = fmaf(G, rj.z, q0);
+                q1 = fmaf(G, rj.w, q1);
+                const float c = w * fmaf(ri.z, rj.z, ri.w * rj.w);
+                p0 = fmaf(c, dx, p0);
+                p1 = fmaf(c, dy, p1);
+            }
+            aq0 += q0; aq1 += q1; ap0 += p0; ap1 += p1;
+        }
+        kq[r][0] = (float)aq0;
+        kq[r][1] = (float)aq1;
+        kp[r][0] = dp_scale * (float)ap0;
+        kp[r][1] = dp_scale * (float)ap1;
+    }
+}
+
+// Write one record into the shared memory of every CTA of the team.
+__device__ __forceinline__ void put_record(const Team& t, float4* rec, int i, float4 v)
+{
+    if (t.cluster) {
+        cg::cluster_group cl = cg::this_cluster();
+        for (int k = 0; k < t.size; ++k) cl.map_shared_rank(rec, k)[i] = v;
+    } else {
+        rec[i] = v;
+    }
+}
+
+// One complete matching of problem b by the team.
+__device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double* s_red, double* s_slot)
+{
+    const BProb P = a.probs[b];
+    const int n = P.n;
+    const int lo = (int)((long long)t.rank * n / t.size), hi = (int)((long long)(t.rank + 1) * n / t.size);
+    const double* X = a.X + 2 * P.off;
+    const double* Y = a.Y + 2 * P.off;
+    double* p0 = a.p0 + 2 * P.off;
+    double* xs = a.xs + 4 * P.off;
+    float* acc = a.acc + 4 * P.off;
+    const float s_f = (float)P.s, dps = (float)P.dp_scale;
+
+    // centre of the bounding box of X (every CTA computes it)
+    double c0x, c0y;
+    {
+        double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+            mnx = fmin(mnx, X[2 * i]); mny = fmin(mny, X[2 * i + 1]);
+            mxx = fmax(mxx, X[2 * i]); mxy = fmax(mxy, X[2 * i + 1]);
+        }
+        const Team solo{0, 1, false};
+        mnx = -team_reduce(solo, -mnx, true, s_red, s_slot);
+        mny = -team_reduce(solo, -mny, true, s_red, s_slot);
+        mxx = team_reduce(solo, mxx, true, s_red, s_slot);
+        mxy = team_reduce(solo, mxy, true, s_red, s_slot);
+        c0x = 0.5 * (mnx + mxx);
+        c0y = 0.5 * (mny + mxy);
+    }
+    float kq[kMaxPerThread][2], kp[kMaxPerThread][2];
+
+    // default gain h = 1 / max_i sum_j G_ij (pair sums at unit momenta (1, 0))
+    double h = P.h;
+    if (!(h > 0.0)) {
+        for (int i = threadIdx.x; i < n; i += kThreads)
+            rec[i] = make_float4((float)((X[2 * i] - c0x) * P.s), (float)((X[2 * i + 1] - c0y) * P.s), 1.0f, 0.0f);
+        __syncthreads();
+        pair_sums(rec, n, lo, hi, P.kernel, dps, kq, kp);
+        double mx = 0.0;
+#pragma unroll
+        for (int r = 0; r < kMaxPerThread; ++r)
+            if (lo + (int)threadIdx.x + r * kThreads < hi) mx = fmax(mx, fabs((double)kq[r][0]));
+        mx = team_reduce(t, mx, true, s_red, s_slot);
+        h = mx > 0.0 ? 1.0 / mx : 1.0;
+    }
+    for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
+        p0[2 * i] = 0.0;
+        p0[2 * i + 1] = 0.0;
+    }
+    team_sync(t);
+
+    const double dt = P.t1 / P.steps;
+    const float dt_f = (float)dt;
+    int status = EP_ENOTCONVERGED, k = 0;
+    double res = 0.0;
+    for (;;) {
+        // shoot from (X, p0): every CTA loads all records itself from global memory
+        for (int i = threadIdx.x; i < n; i += kThreads)
+            rec[i] = make_float4((float)((X[2 * i] - c0x) * P.s), (float)((X[2 * i + 1] - c0y) * P.s),
+                                 (float)__ldcg(p0 + 2 * i), (float)__ldcg(p0 + 2 * i + 1));
+        for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
+            xs[4 * i] = X[2 * i];
+            xs[4 * i + 1] = X[2 * i + 1];
+            xs[4 * i + 2] = p0[2 * i];
+            xs[4 * i + 3] = p0[2 * i + 1];
+        }
+        __syncthreads();
+        float4 xr[kMaxPerThread];  // the thread's particles at the start of the step (scaled)
+#pragma unroll
+        for (int r = 0; r < kMaxPerThread; ++r) {
+            const int i = lo + threadIdx.x + r * kThreads;
+            xr[r] = i < hi ? rec[i] : make_float4(0, 0, 0, 0);
+        }
+        for (int step = 0; step < P.steps; ++step) {
+            for (int stage = 0; stage < 4; ++stage) {
+                pair_sums(rec, n, lo, hi, P.kernel, dps, kq, kp);
+                team_sync(t);  // every CTA has finished reading the stage records
+#pragma unroll
+                for (int r = 0; r < kMaxPerThread; ++r) {
+                    const int i = lo + threadIdx.x + r * kThreads;
+                    if (i >= hi) continue;
+                    float* A = acc + 4 * i;
+                    float4 y;
+                    if (stage < 3) {
+                        const float cdt = (stage == 2 ? 1.0f : 0.5f) * dt_f;
+                        const float bw = stage == 0 ? 1.0f : 2.0f;
+                        y = make_float4(fmaf(cdt * s_f, kq[r][0], xr[r].x), fmaf(cdt * s_f, kq[r][1], xr[r].y),
+                                        fmaf(cdt, kp[r][0], xr[r].z), fmaf(cdt, kp[r][1], xr[r].w));
+                        if (stage == 0) {
+                            A[0] = kq[r][0]; A[1] = kq[r][1]; A[2] = kp[r][0]; A[3] = kp[r][1];
+                        } else {
+                            A[0] = fmaf(bw, kq[r][0], A[0]); A[1] = fmaf(bw, kq[r][1], A[1]);
+                            A[2] = fmaf(bw, kp[r][0], A[2]); A[3] = fmaf(bw, kp[r][1], A[3]);
+                        }
+                    } else {
+                        const float f = dt_f * (1.0f / 6.0f);
+                        double* x = xs + 4 * i;
+                        const double q0 = x[0] + (double)(f * (A[0] + kq[r][0]));
+                        const double q1 = x[1] + (double)(f * (A[1] + kq[r][1]));
+                        const double v0 = x[2] + (double)(f * (A[2] + kp[r][0]));
+                        const double v1 = x[3] + (double)(f * (A[3] + kp[r][1]));
+                        x[0] = q0; x[1] = q1; x[2] = v0; x[3] = v1;
+                        y = make_float4((float)((q0 - c0x) * P.s), (float)((q1 - c0y) * P.s), (float)v0, (float)v1);
+                        xr[r] = y;
+                    }
+                    put_record(t, rec, i, y);
+                }
+                team_sync(t);  // new records visible in every CTA
+            }
+        }
+        // FP64 max-norm residual of Y - Q(1)
+        double mx = 0.0, bad = 0.0;
+        for (int i = lo + threadIdx.x; i < hi; i += kThreads)
+            for (int c = 0; c < 2; ++c) {
+                const double r = Y[2 * i + c] - xs[4 * i + c];
+                if (!isfinite(r)) bad = 1.0;
+                mx = fmax(mx, fabs(r));
+            }
+        bad = team_reduce(t, bad, true, s_red, s_slot);
+        mx = team_reduce(t, mx, true, s_red, s_slot);
+        res = bad > 0.0 ? NAN : mx;
+        if (bad > 0.0) { status = EP_EDIVERGED; break; }
+        if (res < P.eps) { status = EP_OK; break; }
+        if (k == P.maxit) { status = EP_ENOTCONVERGED; break; }
+        // p0 += h (Y - Q(1))   (FP64)
+        for (int i = lo + threadIdx.x; i < hi; i += kThreads)
+            for (int c = 0; c < 2; ++c) p0[2 * i + c] = fma(h, Y[2 * i + c] - xs[4 * i + c], p0[2 * i + c]);
+        ++k;
+        team_sync(t);  // p0 of every slice written before the next shoot reads it
+    }
+    team_sync(t);
+    // H(X, p0) = 1/2 sum_i p_i . (sum_j G_ij p_j)
+    for (int i = threadIdx.x; i < n; i += kThreads)
+        rec[i] = make_float4((float)((X[2 * i] - c0x) * P.s), (float)((X[2 * i + 1] - c0y) * P.s),
+                             (float)__ldcg(p0 + 2 * i), (float)__ldcg(p0 + 2 * i + 1));
+    __syncthreads();
+    pair_sums(rec, n, lo, hi, P.kernel, dps, kq, kp);
+    double hs = 0.0;
+#pragma unroll
+    for (int r = 0; r < kMaxPerThread; ++r) {
+        const int i = lo + threadIdx.x + r * kThreads;
+        if (i < hi) hs += 0.5 * (p0[2 * i] * (double)kq[r][0] + p0[2 * i + 1] * (double)kq[r][1]);
+    }
+    hs = team_reduce(t, hs, false, s_red, s_slot);
+    if (t.rank == 0 && threadIdx.x == 0) {
+        BOut o;
+        o.iters = k;
+        o.status = status;
+        o.resid = res;
+        o.H = hs;
+        o.h = h;
+        a.outs[b] = o;
+    }
+    team_sync(t);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_batched(BArgs a)
+{
+    extern __shared__ float4 rec[];
+    __shared__ double s_red[kThreads / 32];
+    __shared__ double s_slot;
+    __shared__ int s_item;
+    cg::cluster_group cl = cg::this_cluster();
+    const Team team{(int)cl.block_rank(), (int)cl.num_blocks(), true};
+    // team problems: the whole cluster on one problem
+    for (;;) {
+        if (team.rank == 0 && threadIdx.x == 0) s_item = atomicAdd(a.ctr, 1);
+        cl.sync();
+        const int item = *cl.map_shared_rank(&s_item, 0);
+        cl.sync();
+        if (item >= a.nteam) break;
+        solve(a, a.order[item], team, rec, s_red, &s_slot);
+    }
+    // solo problems: every CTA on its own
+    const Team solo{0, 1, false};
+    for (;;) {
+        if (threadIdx.x == 0) s_item = a.nteam + atomicAdd(a.ctr + 1, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.nprob) break;
+        solve(a, a.order[item], solo, rec, s_red, &s_slot);
+    }
+    cl.sync();
+}
+
+bool is_dev(const void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offsets, const double* X,
+                        const double* Y, double* p0, ep_match_info* infos, void* stream)
+{
+    if (nprob < 0) return set_error("ep_match_batched: nprob < 0"), EP_EINVAL;
+    if (nprob == 0) return EP_OK;
+    if (!params || !offsets || !infos) return set_error("ep_match_batched: NULL argument"), EP_EINVAL;
+    if (offsets[0] != 0) return set_error("ep_match_batched: offsets[0] must be 0"), EP_EINVAL;
+    const int team_min = 2048;  // problems at least this large are solved by a whole cluster
+    std::vector<BProb> probs((size_t)nprob);
+    for (int b = 0; b < nprob; ++b) {
+        const ep_params& P = params[b];
+        EP_TRY(check_params(&P));
+        if (P.dim != 2) return set_error("ep_match_batched: problem %d: dim must be 2", b), EP_EINVAL;
+        if (P.precision != EP_MIXED)
+            return set_error("ep_match_batched: problem %d: the batched path runs in mixed precision", b), EP_EINVAL;
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        if (nb < 0 || nb > kMaxN)
+            return set_error("ep_match_batched: problem %d has n = %lld (allowed 0..%d)", b, (long long)nb, kMaxN),
+                   EP_EINVAL;
+        if (nb < team_min && nb > kThreads * kMaxPerThread)
+            return set_error("ep_match_batched: internal size limit"), EP_EINVAL;
+        const ep_match_info& I = infos[b];
+        if (I.maxit < 0 || !(I.eps >= 0.0)) return set_error("ep_match_batched: problem %d: bad maxit/eps", b), EP_EINVAL;
+        const KernelScale ks = kernel_scale(P.kernel, P.sigma);
+        BProb& q = probs[b];
+        q.off = offsets[b];
+        q.n = (int)nb;
+        q.kernel = P.kernel;
+        q.steps = P.steps;
+        q.maxit = I.maxit;
+        q.sigma = P.sigma;
+        q.t1 = P.t1;
+        q.h = I.h;
+        q.eps = I.eps;
+        q.s = ks.s;
+        q.dp_scale = ks.dp_scale;
+    }
+    const int64_t ntot = offsets[nprob];
+    // order: team problems then solo problems, each by decreasing n^2 (LPT)
+    std::vector<int> team, solo;
+    for (int b = 0; b < nprob; ++b) (probs[b].n >= team_min ? team : solo).push_back(b);
+    auto by_cost = [&](int x, int y) { return probs[x].n > probs[y].n || (probs[x].n == probs[y].n && x < y); };
+    std::sort(team.begin(), team.end(), by_cost);
+    std::sort(solo.begin(), solo.end(), by_cost);
+    std::vector<int> order(team);
+    order.insert(order.end(), solo.begin(), solo.end());
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t m = 2 * (size_t)ntot;
+    Sizer z;
+    z.add(sizeof(BProb) * nprob);
+    z.add(sizeof(BOut) * nprob);
+    z.add(sizeof(int) * nprob);
+    z.add(sizeof(int) * 4);
+    z.add(sizeof(double) * 4 * (size_t)ntot);
+    z.add(sizeof(float) * 4 * (size_t)ntot);
+    z.add(sizeof(double) * m * 3);
+    Arena* ar = nullptr;
+    EP_TRY(arena_acquire(st, z.total, &ar));
+    BProb* dprobs = (BProb*)ar->carve(sizeof(BProb) * nprob);
+    BOut* douts = (BOut*)ar->carve(sizeof(BOut) * nprob);
+    int* dorder = (int*)ar->carve(sizeof(int) * nprob);
+    int* dctr = (int*)ar->carve(sizeof(int) * 4);
+    double* xs = (double*)ar->carve(sizeof(double) * 4 * (size_t)ntot + 8);
+    float* acc = (float*)ar->carve(sizeof(float) * 4 * (size_t)ntot + 8);
+    const double* dX = X;
+    const double* dY = Y;
+    double* dp0 = p0;
+    const bool xh = !is_dev(X), yh = !is_dev(Y), ph = !is_dev(p0);
+    if (xh) {
+        double* t = (double*)ar->carve(sizeof(double) * m + 8);
+        EP_TRY_CUDA(cudaMemcpyAsync(t, X, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        dX = t;
+    }
+    if (yh) {
+        double* t = (double*)ar->carve(sizeof(double) * m + 8);
+        EP_TRY_CUDA(cudaMemcpyAsync(t, Y, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        dY = t;
+    }
+    if (ph) dp0 = (double*)ar->carve(sizeof(double) * m + 8);
+    if (!dp0) return set_error("ep_match_batched: workspace too small"), EP_ENOMEM;
+    EP_TRY_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
+    EP_TRY_CUDA(cudaMemsetAsync(dctr, 0, sizeof(int) * 4, st));
+
+    BArgs a{};
+    a.probs = dprobs;
+    a.outs = douts;
+    a.order = dorder;
+    a.nteam = (int)team.size();
+    a.nprob = nprob;
+    a.ctr = dctr;
+    a.X = dX;
+    a.Y = dY;
+    a.p0 = dp0;
+    a.xs = xs;
+    a.acc = acc;
+
+    // persistent grid: as many clusters as can be resident at once
+    const size_t smem = sizeof(float4) * kMaxN;
+    static bool attr = false;
+    if (!attr) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeClusterDimension;
+    attrs[0].val.clusterDim.x = kCluster;
+    attrs[0].val.clusterDim.y = 1;
+    attrs[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    cfg.gridDim = dim3((unsigned)(di.sm_count / kCluster * kCluster));
+    int nclusters = 0;
+    EP_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_batched, &cfg));
+    if (nclusters < 1) return set_error("ep_match_batched: no cluster of %d CTAs fits", kCluster), EP_ECUDA;
+    cfg.gridDim = dim3((unsigned)(nclusters * kCluster));
+    count_launch();
+    EP_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_batched, a));
+
+    std::vector<BOut> outs((size_t)nprob);
+    EP_TRY_CUDA(cudaMemcpyAsync(outs.data(), douts, sizeof(BOut) * nprob, cudaMemcpyDeviceToHost, st));
+    if (ph) EP_TRY_CUDA(cudaMemcpyAsync(p0, dp0, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    EP_TRY_CUDA(cudaGetLastError());
+    ep_status first = EP_OK;
+    for (int b = 0; b < nprob; ++b) {
+        infos[b].iters = outs[b].iters;
+        infos[b].resid_inf = outs[b].resid;
+        infos[b].H = outs[b].H;
+        infos[b].h = outs[b].h;
+        if (first == EP_OK && outs[b].status != EP_OK) first = (ep_status)outs[b].status;
+    }
+    if (first != EP_OK) set_error("ep_match_batched: not every problem converged");
+    return first;
+}
+
+}  // namespace ep

@@ -15,12 +15,13 @@
 // positions would only resolve ~1e-5 sigma.  A pair is accepted iff
 // fmaf(d0, d0, d1 * d1) < 1.0f (the definition ep_cell_neighbors exposes).
 //
-// One stage = bin (cell key + rank by atomics) -> block-wise exclusive scan of the
-// cell counts -> scatter into cell order -> sort each cell by particle index
-// (deterministic sums) -> sweep: each CTA owns an 8 x 8 block of cells, stages the
-// records of its 10 x 10 halo (contiguous row segments of the sorted array) in
-// shared memory, and every thread sums its particles' 3 x 3 neighbour cells in
-// FP32, then applies the RK4 stage.  Stage positions inside a step are
+// One stage = block-wise exclusive scan of the cell counts (the last block scans
+// the block totals) -> scatter into cell order -> sweep: each CTA owns an 8 x 8
+// block of cells, stages the records of its 10 x 10 halo (contiguous row
+// segments of the cell-ordered array) in shared memory, sorts each staged cell by
+// particle index (so sums do not depend on the order atomics gave), and every
+// thread sums its particles' 3 x 3 neighbour cells in FP32, then applies the RK4
+// stage and bins the particle for the next stage (cell count by atomics).  Stage positions inside a step are
 // anchor + c dt k in FP32 on the offsets (re-celled by floor(o / e)); the step
 // state x is FP64 and the anchor is re-derived from it in FP64 every step.
 #include <math.h>
@@ -37,7 +38,7 @@ namespace {
 constexpr int kBlk = 8;                        // cells per sweep block side
 constexpr int kHalo = kBlk + 2;
 constexpr int kSweepThreads = 256;
-constexpr int kSweepCap = 3072;                // halo records staged in shared memory
+constexpr int kSweepCap = 2048;                // halo records staged in shared memory (~2x the mean halo)
 constexpr int kScanBlock = 4096;               // cells per scan block (1024 threads x 4)
 constexpr int kMaxCellsPerAxis2D = 2048;
 
@@ -62,10 +63,12 @@ struct Impl {
     int* rank;
     int* sidx;       // particle index of each sorted slot
     float4* srec;    // records in cell order
-    int* count;      // per cell, then local exclusive scan
+    int* count[2];   // per cell (ping-pong by stage), then local exclusive scan
     int* bsum;       // per scan block total, then exclusive block offsets
+    int* scan_ctr;   // arrival counter of the block scan
     double* bbox;    // min x, min y, max x, max y
     Grid g;
+    int cur;         // count buffer holding the next stage's bins
 };
 
 static_assert(sizeof(Impl) <= 1024, "Impl must fit the CellBufs host block");
@@ -79,10 +82,11 @@ struct Args {
     double dp_scale;
     double sigma;
     Grid g;
-    const int2* cellIn;
-    const int* key;
     const int* count;   // local scan
     const int* boff;    // block offsets
+    int* count_next;    // bins of the next stage (zeroed by this stage's scan)
+    int* key_out;
+    int* rank_out;
     const int* sidx;
     const float4* srec;
     const int2* cellX;
@@ -147,7 +151,8 @@ __global__ void k_bbox2(const double* __restrict__ q, int n, double* out)
 
 // x = (q, p) and the step-start cells / records from FP64.
 __global__ void k_cell_anchor(const double* __restrict__ q, const double* __restrict__ p, int n, Grid g,
-                              double* __restrict__ x, int2* __restrict__ cellX, float4* __restrict__ recX)
+                              double* __restrict__ x, int2* __restrict__ cellX, float4* __restrict__ recX,
+                              int* __restrict__ count, int* __restrict__ key, int* __restrict__ rank)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -165,31 +170,21 @@ __global__ void k_cell_anchor(const double* __restrict__ q, const double* __rest
     locate(qy, 1, g, cy, oy);
     cellX[i] = make_int2(cx, cy);
     recX[i] = make_float4(ox, oy, (float)px, (float)py);
-}
-
-__global__ void k_cell_bin(const int2* __restrict__ cellIn, int n, int ncx, int* __restrict__ count,
-                           int* __restrict__ key, int* __restrict__ rank)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int2 c = cellIn[i];
-    const int k = c.y * ncx + c.x;
+    const int k = cy * g.nc[0] + cx;
     key[i] = k;
     rank[i] = atomicAdd(count + k, 1);
 }
 
-// Exclusive scan of count within blocks of kScanBlock cells; bsum[b] = block total.
-__global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, long long ncell, int* __restrict__ bsum)
+// Exclusive scan of 4 x 1024 values in place (one CTA); returns nothing.
+__device__ void cta_exclusive_scan4(int* __restrict__ v, long long count, int* sw, bool cg)
 {
-    __shared__ int sw[32];
-    const long long base = (long long)blockIdx.x * kScanBlock + 4LL * threadIdx.x;
-    int v[4], s = 0;
+    const long long base = 4LL * threadIdx.x;
+    int x[4], s = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        v[k] = (base + k < ncell) ? count[base + k] : 0;
-        s += v[k];
+        x[k] = (base + k < count) ? (cg ? __ldcg(v + base + k) : v[base + k]) : 0;
+        s += x[k];
     }
-    // inclusive warp scan of the thread totals
     int incl = s;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
@@ -210,44 +205,49 @@ __global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, lo
     int run = incl - s + (w > 0 ? sw[w - 1] : 0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (base + k < ncell) count[base + k] = run;
-        run += v[k];
+        if (base + k < count) v[base + k] = run;
+        run += x[k];
     }
-    if (threadIdx.x == 1023) bsum[blockIdx.x] = run;
 }
 
-// Exclusive scan of the block totals in place (one CTA; at most 1024 x 4 blocks).
-__global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ bsum, int nb)
+// Exclusive scan of the cell counts within blocks of kScanBlock cells; bsum[b] =
+// block total.  The last block to finish scans the block totals into block
+// offsets.  Also zeroes the other count buffer (the next stage's bins).
+__global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, long long ncell, int* __restrict__ bsum,
+                                                     int* __restrict__ zero_next, int* __restrict__ ctr, int nb)
 {
     __shared__ int sw[32];
-    int v[4], s = 0;
+    __shared__ int last;
+    int* blk = count + (long long)blockIdx.x * kScanBlock;
+    const long long cnt = min((long long)kScanBlock, ncell - (long long)blockIdx.x * kScanBlock);
     for (int k = 0; k < 4; ++k) {
-        const int b = 4 * threadIdx.x + k;
-        v[k] = b < nb ? bsum[b] : 0;
-        s += v[k];
+        const long long c = (long long)blockIdx.x * kScanBlock + 4LL * threadIdx.x + k;
+        if (c < ncell) zero_next[c] = 0;
     }
-    int incl = s;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) sw[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        int t = sw[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        sw[lane] = t;
-    }
-    __syncthreads();
-    int run = incl - s + (w > 0 ? sw[w - 1] : 0);
+    // block total first (the scan overwrites the counts)
+    int s = 0;
     for (int k = 0; k < 4; ++k) {
-        const int b = 4 * threadIdx.x + k;
-        if (b < nb) bsum[b] = run;
-        run += v[k];
+        const long long c = 4LL * threadIdx.x + k;
+        if (c < cnt) s += blk[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < 32; ++k) t += sw[k];
+        bsum[blockIdx.x] = t;
+    }
+    __syncthreads();
+    cta_exclusive_scan4(blk, cnt, sw, false);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ctr, 1) == nb - 1);
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        cta_exclusive_scan4(bsum, nb, sw, true);
+        if (threadIdx.x == 0) *ctr = 0;
     }
 }
 
@@ -263,29 +263,9 @@ __global__ void k_cell_scatter(const int* __restrict__ key, const int* __restric
     srec[slot] = recIn[i];
 }
 
-// Sort each cell's slots by particle index (insertion sort; cells hold ~10 particles).
-__global__ void k_cell_sort(const int* __restrict__ count, const int* __restrict__ boff, long long ncell, int n,
-                            int* __restrict__ sidx, float4* __restrict__ srec)
-{
-    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int a = cell_start(count, boff, c);
-    const int b = (c + 1 < ncell) ? cell_start(count, boff, c + 1) : n;
-    for (int u = a + 1; u < b; ++u) {
-        const int ki = sidx[u];
-        const float4 kr = srec[u];
-        int v = u - 1;
-        while (v >= a && sidx[v] > ki) {
-            sidx[v + 1] = sidx[v];
-            srec[v + 1] = srec[v];
-            --v;
-        }
-        sidx[v + 1] = ki;
-        srec[v + 1] = kr;
-    }
-}
-
-__device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, float dpy, int cx, int cy)
+// Finish particle i: RHS output, or the RK4 stage plus the binning of the
+// particle's next-stage cell (key, rank within the cell).
+__device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, float dpy)
 {
     if (a.mode == 1) {
         a.out_q[2 * (size_t)i] = (double)dqx;
@@ -296,6 +276,7 @@ __device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, 
     }
     const float kq0 = dqx, kq1 = dqy, kp0 = a.dp_scale_f * dpx, kp1 = a.dp_scale_f * dpy;
     float* A = a.acc + 4 * (size_t)i;
+    int c0, c1;
     if (a.stage < 3) {
         const float cdt = (a.stage == 2 ? 1.0f : 0.5f) * a.dt_f;
         const float bw = a.stage == 0 ? 1.0f : 2.0f;
@@ -304,7 +285,8 @@ __device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, 
         const float is = (float)a.g.inv_sigma;
         // stage position: anchor offset + c dt kq (units of sigma), re-celled
         float o0 = fmaf(cdt * is, kq0, rx.x), o1 = fmaf(cdt * is, kq1, rx.y);
-        int c0 = ax.x + (int)floorf(o0 / a.g.e[0]), c1 = ax.y + (int)floorf(o1 / a.g.e[1]);
+        c0 = ax.x + (int)floorf(o0 / a.g.e[0]);
+        c1 = ax.y + (int)floorf(o1 / a.g.e[1]);
         c0 = min(max(c0, 0), a.g.nc[0] - 1);
         c1 = min(max(c1, 0), a.g.nc[1] - 1);
         o0 -= (float)(c0 - ax.x) * a.g.e[0];
@@ -325,128 +307,129 @@ __device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, 
         const double q0 = xq[0] + (double)(f * (A[0] + kq0)), q1 = xq[1] + (double)(f * (A[1] + kq1));
         const double p0 = xp[0] + (double)(f * (A[2] + kp0)), p1 = xp[1] + (double)(f * (A[3] + kp1));
         xq[0] = q0; xq[1] = q1; xp[0] = p0; xp[1] = p1;
-        int c0, c1;
         float o0, o1;
         locate(q0, 0, a.g, c0, o0);
         locate(q1, 1, a.g, c1, o1);
         a.cellOut[i] = make_int2(c0, c1);
         a.recOut[i] = make_float4(o0, o1, (float)p0, (float)p1);
     }
-    (void)cx;
-    (void)cy;
+    const int k = c1 * a.g.nc[0] + c0;
+    a.key_out[i] = k;
+    a.rank_out[i] = atomicAdd(a.count_next + k, 1);
 }
 
-// One CTA per 8 x 8 block of cells.
+// One CTA per 8 x 8 block of cells.  Halo cell t = hy * 10 + hx covers grid cell
+// (cx0 - 1 + hx, cy0 - 1 + hy).
 __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
 {
-    __shared__ float4 srec[kSweepCap];
-    __shared__ int hoff[kHalo * kHalo + 1];   // halo cell -> first record (local or global)
-    __shared__ int rowbase[kHalo];
-    __shared__ int own_off[kBlk + 1];         // own particles: prefix over own rows
+    __shared__ float4 s_rec[kSweepCap];
+    __shared__ int s_idx[kSweepCap];
+    __shared__ int c_start[kHalo * kHalo];  // first record (shared index, or global slot)
+    __shared__ int c_len[kHalo * kHalo];
+    __shared__ int c_gs[kHalo * kHalo];     // global slot of the first record
+    __shared__ int own_pre[kBlk * kBlk + 1];
     __shared__ int use_smem;
     const int ncx = a.g.nc[0], ncy = a.g.nc[1];
     const int cx0 = blockIdx.x * kBlk, cy0 = blockIdx.y * kBlk;
-    // halo: rows cy0-1 .. cy0+kBlk, cells cx0-1 .. cx0+kBlk (clipped to the grid)
-    const int xa = max(cx0 - 1, 0), xb = min(cx0 + kBlk, ncx - 1);
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int hy = 0; hy < kHalo; ++hy) {
-            const int row = cy0 - 1 + hy;
-            rowbase[hy] = tot;
-            if (row < 0 || row >= ncy) continue;
-            const long long c_a = (long long)row * ncx + xa, c_b = (long long)row * ncx + xb;
-            const int s0 = cell_start(a.count, a.boff, c_a);
-            const int s1 = (c_b + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c_b + 1) : a.n;
-            tot += s1 - s0;
-        }
-        use_smem = tot <= kSweepCap;
-        // own rows prefix
-        int ot = 0;
-        for (int ly = 0; ly < kBlk; ++ly) {
-            own_off[ly] = ot;
-            const int row = cy0 + ly;
-            if (row >= ncy || cx0 >= ncx) continue;
-            const long long c_a = (long long)row * ncx + cx0;
-            const long long c_b = (long long)row * ncx + min(cx0 + kBlk - 1, ncx - 1);
-            const int s0 = cell_start(a.count, a.boff, c_a);
-            const int s1 = (c_b + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c_b + 1) : a.n;
-            ot += s1 - s0;
-        }
-        own_off[kBlk] = ot;
-    }
-    __syncthreads();
-    const bool sm = use_smem != 0;
-    // per halo cell: first record index (in shared memory, or the global slot)
     for (int t = threadIdx.x; t < kHalo * kHalo; t += kSweepThreads) {
         const int hx = t % kHalo, hy = t / kHalo;
         const int row = cy0 - 1 + hy, col = cx0 - 1 + hx;
-        int v = -1;
+        int gs = 0, len = 0;
         if (row >= 0 && row < ncy && col >= 0 && col < ncx) {
             const long long c = (long long)row * ncx + col;
-            const int g0 = cell_start(a.count, a.boff, c);
-            if (sm) {
-                const int ra = cell_start(a.count, a.boff, (long long)row * ncx + xa);
-                v = rowbase[hy] + (g0 - ra);
-            } else {
-                v = g0;
-            }
+            gs = cell_start(a.count, a.boff, c);
+            const int ge = (c + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c + 1) : a.n;
+            len = ge - gs;
         }
-        hoff[t] = v;
-    }
-    // stage the halo records (contiguous row segments of the sorted array)
-    if (sm) {
-        for (int hy = 0; hy < kHalo; ++hy) {
-            const int row = cy0 - 1 + hy;
-            if (row < 0 || row >= ncy) continue;
-            const long long c_a = (long long)row * ncx + xa, c_b = (long long)row * ncx + xb;
-            const int s0 = cell_start(a.count, a.boff, c_a);
-            const int s1 = (c_b + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c_b + 1) : a.n;
-            for (int u = s0 + threadIdx.x; u < s1; u += kSweepThreads) srec[rowbase[hy] + (u - s0)] = a.srec[u];
-        }
+        c_gs[t] = gs;
+        c_len[t] = len;
     }
     __syncthreads();
-    const float4* base = sm ? srec : a.srec;
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int t = 0; t < kHalo * kHalo; ++t) {
+            c_start[t] = tot;
+            tot += c_len[t];
+        }
+        use_smem = tot <= kSweepCap;
+        if (!use_smem)
+            for (int t = 0; t < kHalo * kHalo; ++t) c_start[t] = c_gs[t];
+        int o = 0;
+        for (int k = 0; k < kBlk * kBlk; ++k) {
+            own_pre[k] = o;
+            o += c_len[((k / kBlk) + 1) * kHalo + (k % kBlk) + 1];
+        }
+        own_pre[kBlk * kBlk] = o;
+    }
+    __syncthreads();
+    const bool sm = use_smem != 0;
+    if (sm) {
+        // stage the halo: the cells of one halo row are contiguous in cell order
+        for (int hy = 0; hy < kHalo; ++hy) {
+            const int t0 = hy * kHalo;
+            const int len = c_start[t0 + kHalo - 1] + c_len[t0 + kHalo - 1] - c_start[t0];
+            int g0 = 0;
+            for (int hx = 0; hx < kHalo; ++hx)
+                if (c_len[t0 + hx] > 0) { g0 = c_gs[t0 + hx] - (c_start[t0 + hx] - c_start[t0]); break; }
+            for (int u = threadIdx.x; u < len; u += kSweepThreads) {
+                s_rec[c_start[t0] + u] = a.srec[g0 + u];
+                s_idx[c_start[t0] + u] = a.sidx[g0 + u];
+            }
+        }
+        __syncthreads();
+        // order each staged cell by particle index (insertion sort; ~10 per cell)
+        for (int t = threadIdx.x; t < kHalo * kHalo; t += kSweepThreads) {
+            const int b0 = c_start[t], b1 = b0 + c_len[t];
+            for (int u = b0 + 1; u < b1; ++u) {
+                const int ki = s_idx[u];
+                const float4 kr = s_rec[u];
+                int v = u - 1;
+                while (v >= b0 && s_idx[v] > ki) {
+                    s_idx[v + 1] = s_idx[v];
+                    s_rec[v + 1] = s_rec[v];
+                    --v;
+                }
+                s_idx[v + 1] = ki;
+                s_rec[v + 1] = kr;
+            }
+        }
+        __syncthreads();
+    }
+    const float4* rec = sm ? s_rec : a.srec;
+    const int* idx = sm ? s_idx : a.sidx;
     const float e0 = a.g.e[0], e1 = a.g.e[1];
-    const int nown = own_off[kBlk];
+    const int nown = own_pre[kBlk * kBlk];
     for (int k = threadIdx.x; k < nown; k += kSweepThreads) {
-        // own particle k: row ly, its global slot and cell
-        int ly = 0;
-        while (own_off[ly + 1] <= k) ++ly;
-        const int row = cy0 + ly;
-        const int sa = cell_start(a.count, a.boff, (long long)row * ncx + cx0);
-        const int slot = sa + (k - own_off[ly]);
-        // find the column: largest col in the own range with start <= slot
-        int col = cx0;
-        const int colmax = min(cx0 + kBlk - 1, ncx - 1);
-        while (col < colmax && cell_start(a.count, a.boff, (long long)row * ncx + col + 1) <= slot) ++col;
-        const float4 ri = a.srec[slot];
-        const int i = a.sidx[slot];
+        // own cell of record k (binary search in the own-cell prefix)
+        int lo = 0, hi = kBlk * kBlk;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (own_pre[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int lx = lo % kBlk, ly = lo / kBlk;
+        const int h = (ly + 1) * kHalo + lx + 1;
+        const int u = c_start[h] + (k - own_pre[lo]);
+        const float4 ri = rec[u];
+        const int i = idx[u];
         float dqx = 0.f, dqy = 0.f, dpx = 0.f, dpy = 0.f;
         int cnt = 0;
         unsigned long long hs = 0ull;
-        const int lx = col - cx0, lyy = row - cy0;
+#pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
-                const int hx = lx + 1 + dx, hy = lyy + 1 + dy;
-                const int h0 = hoff[hy * kHalo + hx];
-                if (h0 < 0) continue;
-                // end of this cell: next cell's start in the same row, or the row/array end
-                const int ccol = col + dx, crow = row + dy;
-                const long long c = (long long)crow * ncx + ccol;
-                const int gs = cell_start(a.count, a.boff, c);
-                const int ge = (c + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c + 1) : a.n;
-                const int len = ge - gs;
+                const int h2 = h + dy * kHalo + dx;
+                const int len = c_len[h2], s0 = c_start[h2];
                 const float sx = __fmul_rn((float)(-dx), e0), sy = __fmul_rn((float)(-dy), e1);
                 for (int v = 0; v < len; ++v) {
-                    const float4 rj = base[h0 + v];
+                    const float4 rj = rec[s0 + v];
                     const float d0 = __fadd_rn(__fsub_rn(ri.x, rj.x), sx);
                     const float d1 = __fadd_rn(__fsub_rn(ri.y, rj.y), sy);
                     const float r2 = __fmaf_rn(d0, d0, __fmul_rn(d1, d1));
                     if (r2 < 1.0f) {
                         if (a.mode == 2) {
                             ++cnt;
-                            const int j = a.sidx[gs + v];
-                            hs += (unsigned long long)(j + 1) * 2654435761ull;
+                            hs += (unsigned long long)(idx[s0 + v] + 1) * 2654435761ull;
                         } else {
                             const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
                             const float G = fmaf(-r2, rs, 1.0f);
@@ -464,7 +447,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
             a.out_cnt[i] = (long long)cnt;
             a.out_hash[i] = hs;
         } else {
-            epilogue(a, i, dqx, dqy, dpx, dpy, col, row);
+            epilogue(a, i, dqx, dqy, dpx, dpy);
         }
     }
 }
@@ -507,30 +490,34 @@ size_t impl_bytes(int n)
     z.add(sizeof(float4) * (size_t)n);
     const size_t maxcell = (size_t)kMaxCellsPerAxis2D * kMaxCellsPerAxis2D;
     z.add(sizeof(int) * maxcell);
+    z.add(sizeof(int) * maxcell);
     z.add(sizeof(int) * (maxcell / kScanBlock + 1));
+    z.add(sizeof(int) * 4);
     z.add(sizeof(double) * 4);
     return z.total;
 }
 
-ep_status run_stage(const ep_params& P, const CellBufs& b, Args a, const int2* cellIn, const float4* recIn,
-                    cudaStream_t st)
+// One stage on the current bins (im->cur): scan, scatter, sweep.  In RK4 mode the
+// sweep bins the next stage into the other count buffer and the bins flip.
+ep_status run_stage(const ep_params& P, const CellBufs& b, Args a, const float4* recIn, cudaStream_t st)
 {
     Impl* im = impl_of(b);
     const Grid& g = im->g;
     const int n = b.n;
     const unsigned gn = (unsigned)((n + 255) / 256);
     const int nb = (int)((g.ncell + kScanBlock - 1) / kScanBlock);
-    EP_TRY_CUDA(cudaMemsetAsync(im->count, 0, sizeof(int) * (size_t)g.ncell, st));
-    count_launch(5);
-    k_cell_bin<<<gn, 256, 0, st>>>(cellIn, n, g.nc[0], im->count, im->key, im->rank);
-    k_scan_local<<<nb, 1024, 0, st>>>(im->count, g.ncell, im->bsum);
-    k_scan_top<<<1, 1024, 0, st>>>(im->bsum, nb);
-    k_cell_scatter<<<gn, 256, 0, st>>>(im->key, im->rank, im->count, im->bsum, recIn, n, im->sidx, im->srec);
-    k_cell_sort<<<(unsigned)((g.ncell + 255) / 256), 256, 0, st>>>(im->count, im->bsum, g.ncell, n, im->sidx, im->srec);
+    int* cnt = im->count[im->cur];
+    int* nxt = im->count[im->cur ^ 1];
+    count_launch(2);
+    k_scan_local<<<nb, 1024, 0, st>>>(cnt, g.ncell, im->bsum, nxt, im->scan_ctr, nb);
+    k_cell_scatter<<<gn, 256, 0, st>>>(im->key, im->rank, cnt, im->bsum, recIn, n, im->sidx, im->srec);
     a.n = n;
     a.g = g;
-    a.count = im->count;
+    a.count = cnt;
     a.boff = im->bsum;
+    a.count_next = nxt;
+    a.key_out = im->key;
+    a.rank_out = im->rank;
     a.sidx = im->sidx;
     a.srec = im->srec;
     a.cellX = im->cellX;
@@ -544,6 +531,7 @@ ep_status run_stage(const ep_params& P, const CellBufs& b, Args a, const int2* c
     count_launch();
     k_cell_sweep<<<grid, kSweepThreads, 0, st>>>(a);
     EP_TRY_CUDA(cudaGetLastError());
+    if (a.mode == 0) im->cur ^= 1;
     return EP_OK;
 }
 
@@ -567,9 +555,12 @@ ep_status load_anchor(const ep_params& P, CellBufs& b, const double* q, const do
     EP_TRY_CUDA(cudaMemcpyAsync(bb, im->bbox, sizeof bb, cudaMemcpyDeviceToHost, st));
     EP_TRY_CUDA(cudaStreamSynchronize(st));
     im->g = make_grid(bb, P.sigma);
+    im->cur = 0;
+    EP_TRY_CUDA(cudaMemsetAsync(im->count[0], 0, sizeof(int) * (size_t)im->g.ncell, st));
+    EP_TRY_CUDA(cudaMemsetAsync(im->scan_ctr, 0, sizeof(int) * 4, st));
     count_launch();
     k_cell_anchor<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, p, n, im->g, write_x ? b.x : nullptr, im->cellX,
-                                                                im->recX);
+                                                                im->recX, im->count[0], im->key, im->rank);
     EP_TRY_CUDA(cudaGetLastError());
     return EP_OK;
 }
@@ -605,8 +596,10 @@ ep_status cell_carve(Arena* ar, int n, int dim, int prec, CellBufs* b)
     im->sidx = (int*)ar->carve(sizeof(int) * (size_t)n);
     im->srec = (float4*)ar->carve(sizeof(float4) * (size_t)n);
     const size_t maxcell = (size_t)kMaxCellsPerAxis2D * kMaxCellsPerAxis2D;
-    im->count = (int*)ar->carve(sizeof(int) * maxcell);
+    im->count[0] = (int*)ar->carve(sizeof(int) * maxcell);
+    im->count[1] = (int*)ar->carve(sizeof(int) * maxcell);
     im->bsum = (int*)ar->carve(sizeof(int) * (maxcell / kScanBlock + 1));
+    im->scan_ctr = (int*)ar->carve(sizeof(int) * 4);
     im->bbox = (double*)ar->carve(sizeof(double) * 4);
     if (!im->bbox) return set_error("workspace too small for the cell list"), EP_ENOMEM;
     return EP_OK;
@@ -627,7 +620,7 @@ ep_status cell_rhs(const ep_params& P, const CellBufs& b, double* dq, double* dp
     a.mode = 1;
     a.out_q = dq;
     a.out_p = dp;
-    return run_stage(P, b, a, im->cellX, im->recX, st);
+    return run_stage(P, b, a, im->recX, st);
 }
 
 ep_status cell_steps(const ep_params& P, const CellBufs& b, int steps, double dt, cudaStream_t st)
@@ -640,11 +633,10 @@ ep_status cell_steps(const ep_params& P, const CellBufs& b, int steps, double dt
     for (int s = 0; s < steps; ++s) {
         for (int stage = 0; stage < 4; ++stage) {
             a.stage = stage;
-            const int2* cin = stage == 0 ? im->cellX : (stage == 2 ? im->cellB : im->cellA);
             const float4* rin = stage == 0 ? im->recX : (stage == 2 ? im->recB : im->recA);
             a.cellOut = stage == 3 ? im->cellX : (stage == 1 ? im->cellB : im->cellA);
             a.recOut = stage == 3 ? im->recX : (stage == 1 ? im->recB : im->recA);
-            EP_TRY(run_stage(P, b, a, cin, rin, st));
+            EP_TRY(run_stage(P, b, a, rin, st));
         }
     }
     return EP_OK;
@@ -699,7 +691,7 @@ ep_status cell_neighbors_entry(const ep_params* params, int64_t n, const double*
     a.mode = 2;
     a.out_cnt = dcnt;
     a.out_hash = dhs;
-    EP_TRY(run_stage(P, b, a, im->cellX, im->recX, st));
+    EP_TRY(run_stage(P, b, a, im->recX, st));
     if (!cdev) EP_TRY_CUDA(cudaMemcpyAsync(count, dcnt, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!hdev) EP_TRY_CUDA(cudaMemcpyAsync(hash, dhs, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, st));
     EP_TRY_CUDA(cudaStreamSynchronize(st));

@@ -1,0 +1,111 @@
+"""ep_match_batched: many independent matchings of uneven size in one persistent
+launch, checked per problem against the FP64 oracle (and the single-problem
+GPU path) through the C ABI.  Mixed precision: momenta <= 1e-4 relative
+(1e-3 for the tent, whose momentum weight jumps at r = sigma)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as o  # noqa: E402
+from paper_1510_03816_gb300 import ep, workloads as w  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_03816_gb300 import build
+
+    build.build()
+    o.build()
+    ep.load()
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def problems(sizes, steps):
+    out = []
+    for b, n in enumerate(sizes):
+        if b % 2 == 0:
+            pr = w.circle_to_ellipse(int(n), stream=2000 + b, sigma=0.2, kernel=ep.TENT, steps=steps)
+        else:
+            pr = w.circle_to_ellipse(int(n), stream=2000 + b, sigma=0.1, kernel=ep.GAUSS, steps=steps)
+        out.append(pr)
+    return out
+
+
+def run_batched(prs, h, eps, maxit, cuda=True):
+    Xs = [torch.tensor(p.X, device="cuda") if cuda else p.X for p in prs]
+    Ys = [torch.tensor(p.Y, device="cuda") if cuda else p.Y for p in prs]
+    prms = [ep.params(dim=2, kernel=p.kernel, sigma=p.sigma, steps=p.steps, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+            for p in prs]
+    return ep.match_batched(Xs, Ys, prms, h=h, eps=eps, maxit=maxit)
+
+
+def test_batched_per_problem_parity_with_oracle():
+    """Solo problems (n < 2048, one CTA each) and team problems (n >= 2048, a whole
+    8-CTA cluster with distributed shared memory) against the oracle."""
+    sizes = [32, 33, 97, 256, 500, 1023, 1500, 2047, 2048, 2600]
+    prs = problems(sizes, steps=4)
+    res = run_batched(prs, 0.0, eps=1e-12, maxit=3)  # default gain per problem
+    for pr, r in zip(prs, res):
+        assert abs(r.h - o.default_gain(pr.X, pr.kernel, pr.sigma)) < 1e-6 * r.h
+        p, st, it, resid, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=r.h, eps=1e-12, maxit=3)
+        assert r.iters == it == 3
+        tol = 1e-3 if pr.kernel == ep.TENT else 1e-4
+        assert rel(r.p0, p) < tol, (pr.n, pr.kernel, rel(r.p0, p))
+        assert abs(r.resid - resid) < tol * resid
+        assert abs(r.H - o.hamiltonian(pr.X, p, pr.kernel, pr.sigma)) < 10 * tol * abs(r.H)
+
+
+def test_batched_default_gain_convergence_and_host_arrays():
+    sizes = [40, 64, 64, 300]
+    prs = problems(sizes, steps=5)
+    res = run_batched(prs, 0.0, eps=5e-3, maxit=60, cuda=False)
+    for pr, r in zip(prs, res):
+        assert abs(r.h - o.default_gain(pr.X, pr.kernel, pr.sigma)) < 1e-6 * r.h
+        p, st, it, resid, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=r.h, eps=5e-3, maxit=60)
+        assert r.status == st and r.iters == it
+        assert rel(r.p0, p) < 1e-3
+
+
+def test_batched_matches_single_problem_path():
+    prs = problems([700, 2100], steps=6)
+    res = run_batched(prs, 0.002, eps=1e-12, maxit=2)
+    for pr, r in zip(prs, res):
+        prm = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=pr.steps, precision=ep.MIXED,
+                        neigh=ep.ALLPAIRS)
+        s = ep.match(torch.tensor(pr.X, device="cuda"), torch.tensor(pr.Y, device="cuda"), prm, h=0.002, eps=1e-12,
+                     maxit=2)
+        assert s.iters == r.iters
+        assert rel(r.p0, s.p0.cpu().numpy()) < 1e-4
+
+
+def test_batched_full_workload_sampled():
+    """The 512-problem workload (n log-uniform in [32, 8192]) with 2 feedback updates;
+    a sample of problems checked against the oracle."""
+    prs = w.batched_curves()
+    res = run_batched(prs, 0.0, eps=1e-12, maxit=2)
+    assert len(res) == 512 and all(r.iters == 2 for r in res)
+    sizes = np.array([p.n for p in prs])
+    under = np.where(sizes < 3000)[0]
+    picks = [int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 2]), int(under[np.argmax(sizes[under])])]
+    for b in picks:
+        pr = prs[b]
+        p, st, it, resid, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=res[b].h, eps=1e-12,
+                                         maxit=2)
+        tol = 1e-3 if pr.kernel == ep.TENT else 1e-4
+        assert rel(res[b].p0, p) < tol
+
+
+def test_batched_invalid_sizes():
+    X = [np.zeros((9000, 2))]
+    with pytest.raises(ep.EPError):
+        ep.match_batched(X, X, [ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=2)], maxit=1)
+    assert ep.match_batched([], [], []) == []
