@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--maxit", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only run warmup + steps shoots of the workload (for ncu captures); no JSON line")
     return ap.parse_args()
@@ -202,7 +203,8 @@ def run_gb300(args):
         total_pairs = float(c.item())
     value = total_pairs / (t_max / 1e3)
 
-    # ---- dominant kernel: the fused all-pairs stage, timed on the launch stream
+    # ---- dominant kernel: the persistent shoot (one cooperative launch per shoot,
+    # 4 x 100 RK4 stages inside), timed on the launch stream
     p_fin = last.p0
     R = 3
     for _ in range(1):
@@ -215,10 +217,10 @@ def run_gb300(args):
     b.record(stream)
     torch.cuda.synchronize()
     shoot_ms = a.elapsed_time(b) / R
-    launch_ms = shoot_ms / (4 * S)
+    launch_ms = shoot_ms
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
-    achieved = FLOPS_PER_PAIR_2D_GAUSS * n * n / (launch_ms / 1e3) / 1e12
+    achieved = FLOPS_PER_PAIR_2D_GAUSS * n * n * 4 * S / (launch_ms / 1e3) / 1e12
 
     # ---- plain FP64 GPU shoot from the same momenta (the comparison point of the shoot metric)
     prm64 = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=S, precision=ep.FP64, neigh=ep.ALLPAIRS)
@@ -253,21 +255,98 @@ def run_gb300(args):
         "shoots_per_s": world * shoots / (t_max / 1e3),
         "endpoint_err_vs_fp64": err,
         "fp64_shoots_per_s": 1e3 / fp64_ms,
-        "roofline": {"bound": "alu", "kernel": "k_stage_mixed<2,GAUSS,1024> (fused all-pairs RK4 stage)",
+        "roofline": {"bound": "alu", "kernel": "k_shoot_mixed<2,GAUSS,1024> (persistent all-pairs shoot, 400 fused RK4 stages per launch)",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": None, "launch_us": launch_ms * 1e3,
+                     "traffic": None, "launch_us": launch_ms * 1e3, "stage_us": launch_ms * 1e3 / (4 * S),
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)",
                      "flops_per_pair": FLOPS_PER_PAIR_2D_GAUSS},
         "e2e": {"value": e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_secondary:
+        out["secondary"] = secondary(ep, workloads, dev, stream, peak_tflops)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(pr, p_fin.cpu().numpy())
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _events_ms(torch, stream, fn, reps):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, r
+
+
+def secondary(ep, workloads, dev, stream, peak_tflops) -> dict:
+    """The other rows of the path, each timed briefly after the main measurement."""
+    import torch
+
+    out = {}
+    hbm = None
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        hbm = 6800.0
+    # cell list: 512 x 512 jittered grid, tent, 32 neighbours on average
+    g = workloads.jittered_grid()
+    Xg = torch.tensor(g.X, device=dev)
+    pg = torch.tensor(0.01 * (g.Y - g.X), device=dev)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=g.sigma, steps=10, precision=ep.MIXED, neigh=ep.CELLLIST)
+    cnt, _, acc_pairs = ep.cell_neighbors(Xg, prm)
+    ms, _ = _events_ms(torch, stream, lambda: ep.shoot(Xg, pg, prm), 3)
+    stage_us = ms * 1e3 / 40
+    byts = 128 * g.n  # algorithmic bytes per particle per stage (state, accumulator, stage copy, keys)
+    out["cell_list"] = {"workload": "jittered_grid 512x512, tent sigma=sqrt(32/(pi N)), RK4 10 steps",
+                        "accepted_pairs_per_stage": acc_pairs, "stage_us": stage_us,
+                        "pair_interactions_per_s": acc_pairs / (stage_us * 1e-6),
+                        "roofline": {"bound": "hbm", "achieved": byts / (stage_us * 1e-6) / 1e9, "peak": hbm,
+                                     "unit": "GB/s", "frac": byts / (stage_us * 1e-6) / 1e9 / hbm,
+                                     "bytes_per_stage": byts, "note": "working set is L2-resident"}}
+    # adjoint: 16384 landmarks in 3-D, Gaussian, 100 steps, checkpoints every 10
+    a3 = workloads.star_surface_3d()
+    X3, Y3, p3 = (torch.tensor(v, device=dev) for v in (a3.X, a3.Y, a3.p0))
+    prm3 = ep.params(dim=3, kernel=ep.GAUSS, sigma=a3.sigma, steps=a3.steps, precision=ep.MIXED)
+    ms, _ = _events_ms(torch, stream, lambda: ep.adjoint(X3, p3, Y3, prm3, a3.lam, 10), 2)
+    pairs = a3.n ** 2 * (4 * a3.steps * 2 + 2)  # forward + recompute RHS (+ G p0 and energy)
+    hvp_pairs = a3.n ** 2 * 4 * a3.steps
+    out["adjoint"] = {"workload": "star_surface_3d N=16384 3-D, Gaussian sigma=0.05, lambda=100, 100 steps, ckpt 10",
+                      "ms_per_gradient": ms, "gradients_per_s": 1e3 / ms,
+                      "rhs_pairs_per_gradient": pairs, "hvp_pairs_per_gradient": hvp_pairs,
+                      "pair_interactions_per_s": (pairs + hvp_pairs) / (ms * 1e-3)}
+    # batched: 512 curve problems, n log-uniform in [32, 8192], maxit capped at 10 here
+    bp = workloads.batched_curves()
+    Xs = [torch.tensor(p.X, device=dev) for p in bp]
+    Ys = [torch.tensor(p.Y, device=dev) for p in bp]
+    prms = [ep.params(dim=2, kernel=p.kernel, sigma=p.sigma, steps=p.steps, precision=ep.MIXED) for p in bp]
+    t0 = time.perf_counter()
+    res = ep.match_batched(Xs, Ys, prms, h=0.0, eps=1e-6, maxit=10)
+    dt = time.perf_counter() - t0
+    bpairs = sum(p.n ** 2 * (4 * p.steps * (r.iters + 1) + 2) for p, r in zip(bp, res))
+    out["batched"] = {"workload": "512 curve problems, n log-uniform [32, 8192], tent 0.2 / Gaussian 0.1, 50 steps, "
+                                  "eps 1e-6, maxit 10 (capped for time)",
+                      "seconds": dt, "matchings_per_s": len(bp) / dt, "pair_interactions_per_s": bpairs / dt,
+                      "converged": sum(1 for r in res if r.status == ep.OK)}
+    # circle -> ellipse, 64 landmarks, tent, FP64 plain method, full Algorithm 1
+    c = workloads.circle_to_ellipse()
+    Xc, Yc = torch.tensor(c.X, device=dev), torch.tensor(c.Y, device=dev)
+    for name, prec in (("fp64", ep.FP64), ("mixed", ep.MIXED)):
+        prmc = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=prec, neigh=ep.ALLPAIRS)
+        t0 = time.perf_counter()
+        r = ep.match(Xc, Yc, prmc, h=0.0, eps=c.eps, maxit=c.maxit)
+        dt = time.perf_counter() - t0
+        out[f"small_{name}"] = {"workload": "circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, maxit 200",
+                                "seconds_per_match": dt, "iters": r.iters, "resid": r.resid,
+                                "shoots_per_s": (r.iters + 1) / dt}
+    return out
 
 
 def cpu_baseline(pr, p0, budget_s: float = 15.0) -> dict:

@@ -19,6 +19,7 @@
 // coordinates (see ep_common.cuh), keeps the step state x_n in FP64 and the
 // RK4 stage combination in FP32; EP_FP64 does every operation in FP64.
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -140,11 +141,11 @@ __device__ void epilogue_mixed(const StageArgs& a, int i)
     // momentum of the stage input (FP32 copy) for the 2-D contraction
     float pin[3];
     if constexpr (DIM == 2) {
-        const float4 v = a.S_in[i];
+        const float4 v = __ldcg(a.S_in + i);
         pin[0] = v.z;
         pin[1] = v.w;
     } else {
-        const float4 v = a.S_in[2 * (size_t)i + 1];
+        const float4 v = __ldcg(a.S_in + 2 * (size_t)i + 1);
         pin[0] = v.x;
         pin[1] = v.y;
         pin[2] = v.z;
@@ -239,13 +240,16 @@ __device__ void epilogue_mixed(const StageArgs& a, int i)
     }
 }
 
-template <int DIM, int KER, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
+// The pair phase of one stage over this CTA's stream-K range: per tile segment,
+// stage the sources in shared memory, sum in registers, reduce over warps and
+// add into the FP64 accumulator K.  With LAST the last CTA to reach a tile also
+// applies the RK4 stage to it (one launch per stage); without LAST the caller
+// finishes the particles after a grid-wide barrier (persistent shoot).
+template <int DIM, int KER, int THREADS, bool LAST>
+__device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, int* s_last)
 {
     constexpr int W = THREADS / 32;
     constexpr int V = DIM == 2 ? 1 : 2;  // float4 per particle
-    extern __shared__ float4 smem[];
-    __shared__ int s_last;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = a.n;
@@ -264,10 +268,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
             const int i = b * kTileI + lane + 32 * r;
             if (i < n) {
                 if constexpr (DIM == 2) {
-                    const float4 v = a.S_in[i];
+                    const float4 v = __ldcg(a.S_in + i);
                     qi[r][0] = v.x; qi[r][1] = v.y; pi[r][0] = v.z; pi[r][1] = v.w;
                 } else {
-                    const float4 v0 = a.S_in[2 * (size_t)i], v1 = a.S_in[2 * (size_t)i + 1];
+                    const float4 v0 = __ldcg(a.S_in + 2 * (size_t)i), v1 = __ldcg(a.S_in + 2 * (size_t)i + 1);
                     qi[r][0] = v0.x; qi[r][1] = v0.y; qi[r][2] = v0.z;
                     pi[r][0] = v1.x; pi[r][1] = v1.y; pi[r][2] = v1.z;
                 }
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
         for (int cj = j0; cj < j1; cj += kChunk) {
             const int L = min(kChunk, j1 - cj);
             __syncthreads();
-            for (int t = threadIdx.x; t < L * V; t += THREADS) smem[t] = a.S_in[(size_t)cj * V + t];
+            for (int t = threadIdx.x; t < L * V; t += THREADS) smem[t] = __ldcg(a.S_in + (size_t)cj * V + t);
             __syncthreads();
             const int ja = warp * L / W, jb = (warp + 1) * L / W;
 #pragma unroll 4
@@ -343,22 +347,222 @@ __global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
             const int i = b * kTileI + il;
             if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, (double)s);
         }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int prev = atomicAdd(a.counters + b, 1);
-            s_last = (prev == tile_contributors(b, a) - 1);
-        }
-        __syncthreads();
-        if (s_last) {
+        if constexpr (LAST) {
             __threadfence();
-            if (threadIdx.x < kTileI) {
-                const int i = b * kTileI + threadIdx.x;
-                if (i < n) epilogue_mixed<DIM>(a, i);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int prev = atomicAdd(a.counters + b, 1);
+                *s_last = (prev == tile_contributors(b, a) - 1);
             }
-            if (threadIdx.x == 0) a.counters[b] = 0;
+            __syncthreads();
+            if (*s_last) {
+                __threadfence();
+                if (threadIdx.x < kTileI) {
+                    const int i = b * kTileI + threadIdx.x;
+                    if (i < n) epilogue_mixed<DIM>(a, i);
+                }
+                if (threadIdx.x == 0) a.counters[b] = 0;
+            }
         }
         u0 += (j1 - j0);
+    }
+}
+
+// ------------------------------------------------------------------ 2-D Gaussian, factored
+// The pair phase of the 2-D Gaussian in tiles of kTileG = 128 particles (32 lanes
+// x 4 registers), on coordinates centred on the tile's first particle,
+// q'' = q' - q'_first.  With G = 2^-|q''_i - q''_j|^2 (scaled units),
+//   G_ij = 2^-|q''_i|^2 * 2^t,   t = 2 q''_i . q''_j - |q''_j|^2  (<= |q''_i|^2),
+//   dq_i = E_i sum_j g_ij p_j,   M_i = q''_i (x) dq_i - E_i sum_j g_ij (q''_j (x) p_j),
+// with g = 2^t and E_i = 2^-|q''_i|^2, so a pair costs two FMAs for t, one ex2 and
+// six FMAs, against per-source records (2x, 2y, -|q''|^2, px), (py, x px, x py,
+// y px), (y py) built once per staged chunk.  t never exceeds |q''_i|^2; a tile
+// whose |q''_i|^2 could overflow (> kFactorMax) takes the difference form
+// d = q''_i - q''_j instead (same records).
+constexpr int kTileG = 128;
+constexpr int kChunkG = 2048;
+constexpr float kFactorMax = 60.0f;
+
+template <int THREADS>
+__device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* smem)
+{
+    constexpr int W = THREADS / 32;
+    constexpr int RI = kTileG / 32;
+    float4* recA = smem;                                         // [2 * kChunkG]
+    float* recB = reinterpret_cast<float*>(smem + 2 * kChunkG);  // [kChunkG]
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n = a.n;
+    long long u0 = (long long)blockIdx.x * a.U / a.G;
+    const long long u1 = (long long)(blockIdx.x + 1) * a.U / a.G;
+    while (u0 < u1) {
+        const int b = (int)(u0 / n);
+        const int j0 = (int)(u0 - (long long)b * n);
+        const int j1 = (int)min((long long)n, (long long)j0 + (u1 - u0));
+        const float4 c4 = __ldcg(a.S_in + (size_t)b * kTileG);  // tile centre: its first particle
+        float qx[RI], qy[RI];
+        float mq = 0.0f;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int i = b * kTileG + lane + 32 * r;
+            const float4 v = i < n ? __ldcg(a.S_in + i) : c4;
+            qx[r] = v.x - c4.x;
+            qy[r] = v.y - c4.y;
+            mq = fmaxf(mq, fmaf(qx[r], qx[r], qy[r] * qy[r]));
+        }
+        const bool factored = !__syncthreads_or(mq > kFactorMax);
+        float sq0[RI], sq1[RI], sb[RI][4];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            sq0[r] = sq1[r] = 0.0f;
+            sb[r][0] = sb[r][1] = sb[r][2] = sb[r][3] = 0.0f;
+        }
+        for (int cj = j0; cj < j1; cj += kChunkG) {
+            const int L = min(kChunkG, j1 - cj);
+            __syncthreads();
+            for (int t = threadIdx.x; t < L; t += THREADS) {
+                const float4 v = __ldcg(a.S_in + cj + t);
+                const float x = v.x - c4.x, y = v.y - c4.y;
+                recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), v.z);
+                recA[2 * t + 1] = make_float4(v.w, x * v.z, x * v.w, y * v.z);
+                recB[t] = y * v.w;
+            }
+            __syncthreads();
+            const int ja = warp * L / W, jb = (warp + 1) * L / W;
+            if (factored) {
+#pragma unroll 2
+                for (int j = ja; j < jb; ++j) {
+                    const float4 A = recA[2 * j], B = recA[2 * j + 1];
+                    const float byy = recB[j];
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const float g = ex2_approx(fmaf(qx[r], A.x, fmaf(qy[r], A.y, A.z)));
+                        sq0[r] = fmaf(g, A.w, sq0[r]);
+                        sq1[r] = fmaf(g, B.x, sq1[r]);
+                        sb[r][0] = fmaf(g, B.y, sb[r][0]);
+                        sb[r][1] = fmaf(g, B.z, sb[r][1]);
+                        sb[r][2] = fmaf(g, B.w, sb[r][2]);
+                        sb[r][3] = fmaf(g, byy, sb[r][3]);
+                    }
+                }
+            } else {
+                // difference form: G = ex2(-|d|^2) with d = q''_i - q''_j, same sums
+                for (int j = ja; j < jb; ++j) {
+                    const float4 A = recA[2 * j], B = recA[2 * j + 1];
+                    const float byy = recB[j];
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const float dx = fmaf(-0.5f, A.x, qx[r]), dy = fmaf(-0.5f, A.y, qy[r]);
+                        const float G = ex2_approx(-fmaf(dx, dx, dy * dy));
+                        sq0[r] = fmaf(G, A.w, sq0[r]);
+                        sq1[r] = fmaf(G, B.x, sq1[r]);
+                        sb[r][0] = fmaf(G, B.y, sb[r][0]);
+                        sb[r][1] = fmaf(G, B.z, sb[r][1]);
+                        sb[r][2] = fmaf(G, B.w, sb[r][2]);
+                        sb[r][3] = fmaf(G, byy, sb[r][3]);
+                    }
+                }
+            }
+        }
+        // per particle: dq = E sq, M = q'' (x) dq - E sb  (E = 1 in the difference form)
+        __syncthreads();
+        float* red = reinterpret_cast<float*>(smem);  // [W][6][kTileG]
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
+            const float d0 = E * sq0[r], d1 = E * sq1[r];
+            float* o = red + (size_t)warp * kKWidth * kTileG + lane + 32 * r;
+            o[0 * kTileG] = d0;
+            o[1 * kTileG] = d1;
+            o[2 * kTileG] = fmaf(qx[r], d0, -E * sb[r][0]);
+            o[3 * kTileG] = fmaf(qx[r], d1, -E * sb[r][1]);
+            o[4 * kTileG] = fmaf(qy[r], d0, -E * sb[r][2]);
+            o[5 * kTileG] = fmaf(qy[r], d1, -E * sb[r][3]);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kKWidth * kTileG; t += THREADS) {
+            const int k = t / kTileG, il = t % kTileG;
+            float sum = 0.0f;
+#pragma unroll 8
+            for (int w2 = 0; w2 < W; ++w2) sum += red[(w2 * kKWidth + k) * kTileG + il];
+            const int i = b * kTileG + il;
+            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, (double)sum);
+        }
+        u0 += (j1 - j0);
+    }
+}
+
+template <int DIM, int KER, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
+{
+    extern __shared__ float4 smem[];
+    __shared__ int s_last;
+    stage_pairs<DIM, KER, THREADS, true>(a, smem, &s_last);
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident).  The counter
+// only grows: barrier number e completes when it reaches e * gridDim.x.  The
+// wait is bounded; on giving up it raises the shared error flag, and every CTA
+// that sees the flag returns false so the kernel ends instead of hanging.
+constexpr long long kSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_barrier(unsigned* bar, int* err, unsigned epoch)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned target = epoch * gridDim.x;
+        long long spins = 0;
+        while (ld_acquire_u32(bar) < target) {
+            if ((++spins & 63) == 0 && *(volatile int*)err) { ok = 0; break; }
+            if (spins > kSpinLimit) {
+                atomicExch(err, 1);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// A whole shoot of `steps` RK4 steps in one cooperative launch: per stage, the
+// pair phase, a barrier, the RK4 stage of the particles this CTA owns
+// ([c n / G, (c+1) n / G)), and a barrier.
+template <int DIM, int KER, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_shoot_mixed(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
+{
+    extern __shared__ float4 smem[];
+    const int n = a.n;
+    const int i0 = (int)((long long)blockIdx.x * n / gridDim.x), i1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
+    unsigned epoch = 0;
+    a.Sx = Sx;
+    for (int s = 0; s < steps; ++s) {
+        for (int stage = 0; stage < 4; ++stage) {
+            a.stage = stage;
+            a.S_in = stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
+            a.S_out = stage == 1 ? Sb : Sa;
+            if constexpr (DIM == 2 && KER == EP_GAUSS) {
+                stage_pairs_gauss2<THREADS>(a, smem);
+            } else {
+                stage_pairs<DIM, KER, THREADS, false>(a, smem, nullptr);
+            }
+            if (!grid_barrier(bar, err, ++epoch)) return;
+            for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<DIM>(a, i);
+            if (!grid_barrier(bar, err, ++epoch)) return;
+        }
     }
 }
 
@@ -629,6 +833,18 @@ ep_status launch_stage(const ep_params& P, const StageArgs& a, int threads, cuda
     return EP_EINVAL;
 }
 
+// EP_PERSISTENT=0 in the environment selects one launch per RK4 stage instead of
+// the persistent shoot (both compute the same result).
+bool allpairs_persistent_enabled()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("EP_PERSISTENT");
+        v = (e && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 StageArgs base_args(const ep_params& P, const AllPairsBufs& b, const APConfig& cfg)
 {
     StageArgs a{};
@@ -660,6 +876,7 @@ size_t allpairs_bytes(int n, int dim, int prec)
     z.add(sizeof(double) * kKWidth * (size_t)n);   // K
     z.add(sizeof(int) * (size_t)ntiles);           // counters
     z.add(sizeof(double) * 4);                     // c0
+    z.add(sizeof(unsigned) * 4);                   // barrier counter, error flag
     if (prec == EP_MIXED) {
         const int V = dim == 2 ? 1 : 2;
         for (int k = 0; k < 3; ++k) z.add(sizeof(float4) * V * (size_t)n);
@@ -681,6 +898,8 @@ ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b)
     b->K = (double*)ar->carve(sizeof(double) * kKWidth * (size_t)n);
     b->counters = (int*)ar->carve(sizeof(int) * (size_t)ntiles);
     b->c0 = (double*)ar->carve(sizeof(double) * 4);
+    b->bar = (unsigned*)ar->carve(sizeof(unsigned) * 4);
+    b->err = (int*)(b->bar ? b->bar + 1 : nullptr);
     if (prec == EP_MIXED) {
         const int V = dim == 2 ? 1 : 2;
         b->Sx = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
@@ -755,6 +974,66 @@ ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, do
     return EP_OK;
 }
 
+template <int DIM, int KER>
+ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done)
+{
+    constexpr int THREADS = 1024;
+    constexpr int W = THREADS / 32;
+    constexpr int V = DIM == 2 ? 1 : 2;
+    constexpr bool kFact = DIM == 2 && KER == EP_GAUSS;
+    const size_t smem = kFact ? std::max((size_t)kChunkG * (2 * sizeof(float4) + sizeof(float)),
+                                         (size_t)W * kKWidth * kTileG * sizeof(float))
+                              : std::max((size_t)kChunk * V * sizeof(float4), (size_t)W * kKWidth * kTileI * sizeof(float));
+    auto fn = k_shoot_mixed<DIM, KER, THREADS>;
+    static int resident = -1;
+    if (resident < 0) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, smem));
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        resident = per_sm * di.sm_count;
+    }
+    *done = false;
+    if (a0.G > resident) return EP_OK;  // not all CTAs can be resident: per-stage launches instead
+    StageArgs a = a0;
+    if (kFact) {
+        // tiles of kTileG particles: units and CTA count of that decomposition
+        a.U = (long long)((b.n + kTileG - 1) / kTileG) * b.n;
+        a.G = (int)std::min<long long>(a.G, a.U);
+    }
+    const float4* Sx = b.Sx;
+    float4* Sa = b.Sa;
+    float4* Sb = b.Sb;
+    unsigned* bar = b.bar;
+    int* err = b.err;
+    EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 2, st));
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
+    count_launch();
+    EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
+    int herr = 0;
+    EP_TRY_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("persistent shoot: a grid-barrier wait gave up (kernel ended early)");
+        return EP_ETIMEOUT;
+    }
+    *done = true;
+    return EP_OK;
+}
+
+ep_status launch_shoot(const ep_params& P, const StageArgs& a, const AllPairsBufs& b, int steps, cudaStream_t st,
+                       bool* done)
+{
+#define EP_SHOOT_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) return launch_shoot_mixed<D, K>(a, b, steps, st, done);
+    EP_SHOOT_CASE(2, EP_GAUSS) EP_SHOOT_CASE(2, EP_TENT) EP_SHOOT_CASE(2, EP_EXPCONE)
+    EP_SHOOT_CASE(3, EP_GAUSS) EP_SHOOT_CASE(3, EP_TENT) EP_SHOOT_CASE(3, EP_EXPCONE)
+#undef EP_SHOOT_CASE
+    *done = false;
+    return EP_OK;
+}
+
 ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt, cudaStream_t st)
 {
     if (b.n == 0 || steps == 0) return EP_OK;
@@ -763,6 +1042,12 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
     a.mode = MODE_RK4;
     a.dt = dt;
     a.dt_f = (float)dt;
+    if (P.precision == EP_MIXED && cfg.threads == 1024 && allpairs_persistent_enabled()) {
+        a.Sx_w = b.Sx;
+        bool done = false;
+        EP_TRY(launch_shoot(P, a, b, steps, st, &done));
+        if (done) return EP_OK;
+    }
     a.Sx = b.Sx;
     a.Sx_w = b.Sx;
     for (int s = 0; s < steps; ++s) {

@@ -15,6 +15,8 @@ struct AllPairsBufs {
     double* K = nullptr;     // FP64 k accumulator, n * kKWidth, zero between launches
     int* counters = nullptr; // per-tile arrival counters, zero between launches
     double* c0 = nullptr;    // origin of the scaled coordinates (3 doubles)
+    unsigned* bar = nullptr; // grid-barrier counter of the persistent shoot
+    int* err = nullptr;      // error flag of the persistent shoot (1 = a barrier wait gave up)
     // mixed
     float4* Sx = nullptr;    // step-start stage copy (stage-0 input)
     float4* Sa = nullptr;    // stage copies (ping-pong)
