@@ -22,6 +22,9 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "ep_allpairs.cuh"
 
@@ -399,13 +402,29 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
         const int b = (int)(u0 / n);
         const int j0 = (int)(u0 - (long long)b * n);
         const int j1 = (int)min((long long)n, (long long)j0 + (u1 - u0));
+        // issue every load of the segment start at once: the tile centre, the
+        // lane's particles and the first chunk's sources (kChunkG / THREADS each)
+        constexpr int PF = kChunkG / THREADS;
+        const int L0 = min(kChunkG, j1 - j0);
+        float4 pre[PF];
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int t = threadIdx.x + k * THREADS;
+            pre[k] = t < L0 ? __ldcg(a.S_in + j0 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const float4 c4 = __ldcg(a.S_in + (size_t)b * kTileG);  // tile centre: its first particle
+        float4 vi[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int i = b * kTileG + lane + 32 * r;
+            vi[r] = i < n ? __ldcg(a.S_in + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         float qx[RI], qy[RI];
         float mq = 0.0f;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
             const int i = b * kTileG + lane + 32 * r;
-            const float4 v = i < n ? __ldcg(a.S_in + i) : c4;
+            const float4 v = i < n ? vi[r] : c4;
             qx[r] = v.x - c4.x;
             qy[r] = v.y - c4.y;
             mq = fmaxf(mq, fmaf(qx[r], qx[r], qy[r] * qy[r]));
@@ -421,7 +440,7 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
             const int L = min(kChunkG, j1 - cj);
             __syncthreads();
             for (int t = threadIdx.x; t < L; t += THREADS) {
-                const float4 v = __ldcg(a.S_in + cj + t);
+                const float4 v = cj == j0 ? pre[t / THREADS] : __ldcg(a.S_in + cj + t);
                 const float x = v.x - c4.x, y = v.y - c4.y;
                 recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), v.z);
                 recA[2 * t + 1] = make_float4(v.w, x * v.z, x * v.w, y * v.z);
@@ -515,23 +534,32 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
 
 __device__ bool grid_barrier(unsigned* bar, int* err, unsigned epoch)
 {
+    // bar[0..7]: arrival counters, CTA c arrives on bar[c % 8] (spreads the atomics
+    // over eight L2 lines); barrier e completes when bar[k] reaches e * (CTAs on k)
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned G = gridDim.x;
+        if (lane == 0) {
+            __threadfence();
+            atomicAdd(bar + (blockIdx.x & 7), 1u);
+        }
+        const unsigned mine = lane < 8 ? (G / 8 + ((unsigned)lane < (G & 7) ? 1u : 0u)) : 0u;
+        const unsigned target = epoch * mine;
         int ok = 1;
-        __threadfence();
-        atomicAdd(bar, 1u);
-        const unsigned target = epoch * gridDim.x;
         long long spins = 0;
-        while (ld_acquire_u32(bar) < target) {
+        for (;;) {
+            const unsigned v = lane < 8 ? ld_acquire_u32(bar + lane) : 0u;
+            if (__all_sync(0xffffffffu, v >= target)) break;
             if ((++spins & 63) == 0 && *(volatile int*)err) { ok = 0; break; }
             if (spins > kSpinLimit) {
-                atomicExch(err, 1);
+                if (lane == 0) atomicExch(err, 1);
                 ok = 0;
                 break;
             }
         }
-        s_ok = ok;
+        if (lane == 0) s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -876,7 +904,11 @@ size_t allpairs_bytes(int n, int dim, int prec)
     z.add(sizeof(double) * kKWidth * (size_t)n);   // K
     z.add(sizeof(int) * (size_t)ntiles);           // counters
     z.add(sizeof(double) * 4);                     // c0
-    z.add(sizeof(unsigned) * 4);                   // barrier counter, error flag
+    z.add(sizeof(unsigned) * 12);                  // barrier counters, error flag
+    if (prec == EP_MIXED && dim == 2) {
+        z.add(sizeof(double) * 2 * dim * (size_t)n);  // tuner backup of x
+        z.add(sizeof(float4) * (size_t)n);            // tuner backup of the stage copy
+    }
     if (prec == EP_MIXED) {
         const int V = dim == 2 ? 1 : 2;
         for (int k = 0; k < 3; ++k) z.add(sizeof(float4) * V * (size_t)n);
@@ -898,8 +930,12 @@ ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b)
     b->K = (double*)ar->carve(sizeof(double) * kKWidth * (size_t)n);
     b->counters = (int*)ar->carve(sizeof(int) * (size_t)ntiles);
     b->c0 = (double*)ar->carve(sizeof(double) * 4);
-    b->bar = (unsigned*)ar->carve(sizeof(unsigned) * 4);
-    b->err = (int*)(b->bar ? b->bar + 1 : nullptr);
+    b->bar = (unsigned*)ar->carve(sizeof(unsigned) * 12);
+    b->err = (int*)(b->bar ? b->bar + 8 : nullptr);
+    if (prec == EP_MIXED && dim == 2) {
+        b->x_bak = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
+        b->S_bak = (float4*)ar->carve(sizeof(float4) * (size_t)n);
+    }
     if (prec == EP_MIXED) {
         const int V = dim == 2 ? 1 : 2;
         b->Sx = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
@@ -932,10 +968,11 @@ APConfig allpairs_config(int n, int dim, int prec, int kernel)
         c.threads = 256;
         c.ctas = di.sm_count * 4;
     }
-    // keep at least ~256 units (pairs per lane-pair) per CTA for tiny problems
+    // keep at least ~256 units (mixed) or ~16 units (FP64, whose pairs cost ~60x more)
+    // per CTA for tiny problems
     const long long ntiles = (n + kTileI - 1) / kTileI;
     const long long U = ntiles * (long long)n;
-    const long long maxc = std::max<long long>(1, U / 256);
+    const long long maxc = std::max<long long>(1, U / (prec == EP_MIXED ? 256 : 16));
     c.ctas = (int)std::max<long long>(1, std::min<long long>(c.ctas, maxc));
     return c;
 }
@@ -975,7 +1012,8 @@ ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, do
 }
 
 template <int DIM, int KER>
-ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done)
+ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
+                             cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
 {
     constexpr int THREADS = 1024;
     constexpr int W = THREADS / 32;
@@ -1007,10 +1045,12 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
     float4* Sb = b.Sb;
     unsigned* bar = b.bar;
     int* err = b.err;
-    EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 2, st));
+    EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
     void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
     count_launch();
+    if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
+    if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
     int herr = 0;
     EP_TRY_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     EP_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1023,14 +1063,86 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
 }
 
 ep_status launch_shoot(const ep_params& P, const StageArgs& a, const AllPairsBufs& b, int steps, cudaStream_t st,
-                       bool* done)
+                       bool* done, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
 {
 #define EP_SHOOT_CASE(D, K) \
-    if (P.dim == D && P.kernel == K) return launch_shoot_mixed<D, K>(a, b, steps, st, done);
+    if (P.dim == D && P.kernel == K) return launch_shoot_mixed<D, K>(a, b, steps, st, done, ev0, ev1);
     EP_SHOOT_CASE(2, EP_GAUSS) EP_SHOOT_CASE(2, EP_TENT) EP_SHOOT_CASE(2, EP_EXPCONE)
     EP_SHOOT_CASE(3, EP_GAUSS) EP_SHOOT_CASE(3, EP_TENT) EP_SHOOT_CASE(3, EP_EXPCONE)
 #undef EP_SHOOT_CASE
     *done = false;
+    return EP_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// The persistent 2-D Gaussian shoot splits the pair matrix (tiles of kTileG x n)
+// over G CTAs.  G = SM count balances the work exactly but lets some CTAs span two
+// tiles (each segment start costs a round of loads and a reduction); a G that is a
+// multiple of the tile count keeps every CTA inside one tile at the price of idle
+// SMs.  The tuner times a one-step shoot for each candidate on the loaded state
+// (restoring it afterwards) and caches the fastest per (n, dim, kernel).
+// EP_AUTOTUNE=0 in the environment skips it (G = SM count).
+struct TuneKey {
+    int n, dim, kernel, dev;
+    bool operator<(const TuneKey& o) const
+    {
+        return n != o.n ? n < o.n : dim != o.dim ? dim < o.dim : kernel != o.kernel ? kernel < o.kernel : dev < o.dev;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+bool autotune_enabled()
+{
+    const char* e = getenv("EP_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a, double dt, cudaStream_t st, int* best)
+{
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    const int sm = di.sm_count;
+    const int ntiles = (b.n + kTileG - 1) / kTileG;
+    // the default split, the full and 7/8 SM counts, the two largest tile-aligned counts
+    std::vector<int> cand = {a.G, sm, sm - sm / 8};
+    for (int k = sm / std::max(1, ntiles), c = 0; k >= 1 && c < 2; --k, ++c) cand.push_back(ntiles * k);
+    for (int& g : cand) g = (int)std::min<long long>(g, a.U);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    const size_t m2 = 2 * (size_t)P.dim * b.n;
+    EP_TRY_CUDA(cudaMemcpyAsync(b.x_bak, b.x, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(b.S_bak, b.Sx, sizeof(float4) * (size_t)b.n, cudaMemcpyDeviceToDevice, st));
+    cudaEvent_t e0, e1;
+    EP_TRY_CUDA(cudaEventCreate(&e0));
+    EP_TRY_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = sm;
+    a.dt = dt;
+    a.dt_f = (float)dt;
+    for (int G : cand) {
+        if (G < 1) continue;
+        a.G = G;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            EP_TRY_CUDA(cudaMemcpyAsync(b.x, b.x_bak, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
+            EP_TRY_CUDA(cudaMemcpyAsync(b.Sx, b.S_bak, sizeof(float4) * (size_t)b.n, cudaMemcpyDeviceToDevice, st));
+            bool done = false;
+            ep_status s = launch_shoot(P, a, b, 1, st, &done, e0, e1);
+            if (s != EP_OK || !done) break;
+            float t = 0.f;
+            EP_TRY_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = G;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    EP_TRY_CUDA(cudaMemcpyAsync(b.x, b.x_bak, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(b.Sx, b.S_bak, sizeof(float4) * (size_t)b.n, cudaMemcpyDeviceToDevice, st));
     return EP_OK;
 }
 
@@ -1044,6 +1156,23 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
     a.dt_f = (float)dt;
     if (P.precision == EP_MIXED && cfg.threads == 1024 && allpairs_persistent_enabled()) {
         a.Sx_w = b.Sx;
+        if (P.dim == 2 && P.kernel == EP_GAUSS && b.x_bak && autotune_enabled()) {
+            DeviceInfo di{};
+            EP_TRY(device_info(&di));
+            const TuneKey key{b.n, P.dim, P.kernel, di.device};
+            int G = -1;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) G = it->second;
+            }
+            if (G < 0) {
+                EP_TRY(tune_persistent(P, b, a, dt, st, &G));
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tuned[key] = G;
+            }
+            a.G = G;
+        }
         bool done = false;
         EP_TRY(launch_shoot(P, a, b, steps, st, &done));
         if (done) return EP_OK;

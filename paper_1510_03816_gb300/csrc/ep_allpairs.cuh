@@ -17,6 +17,8 @@ struct AllPairsBufs {
     double* c0 = nullptr;    // origin of the scaled coordinates (3 doubles)
     unsigned* bar = nullptr; // grid-barrier counter of the persistent shoot
     int* err = nullptr;      // error flag of the persistent shoot (1 = a barrier wait gave up)
+    double* x_bak = nullptr; // autotuner backups of x and the stage copy (2-D mixed only)
+    float4* S_bak = nullptr;
     // mixed
     float4* Sx = nullptr;    // step-start stage copy (stage-0 input)
     float4* Sa = nullptr;    // stage copies (ping-pong)
