@@ -95,7 +95,8 @@ ep_status ep_shoot(const ep_params* params, int64_t n, const double* q0, const d
  * stop if max|r| < eps; p0 += h r } at most info->maxit updates.  p0: in = initial
  * guess (zeros for the paper's default, Note 1 item 4), out = last iterate.  The
  * residual and the update are FP64 in both precisions.  Synchronises the stream
- * (the stopping test is read on the host each iteration).  Returns EP_OK,
+ * (the stopping test is read on the host each iteration; small 2-D mixed-precision
+ * problems, n <= 384, run the whole loop on one CTA of the batched solver).  Returns EP_OK,
  * EP_ENOTCONVERGED or EP_EDIVERGED; info is filled in all three cases. */
 ep_status ep_match(const ep_params* params, int64_t n, const double* X, const double* Y,
                    double* p0, ep_match_info* info, void* stream);
@@ -112,8 +113,9 @@ ep_status ep_adjoint(const ep_params* params, int64_t n, const double* X, const 
 
 /* nprob independent matchings in one persistent launch.  Problem b has
  * n_b = offsets[b+1] - offsets[b] particles stored at rows offsets[b] .. of X, Y and
- * p0 (all (offsets[nprob], dim)); params[b] and infos[b] are its parameters and
- * result (host arrays; infos[b].hist is ignored).  offsets: host array of nprob+1
+ * p0 (all (offsets[nprob], dim)); p0 holds the initial guesses on entry and the last
+ * iterates on return.  params[b] and infos[b] are its parameters and result (host
+ * arrays; infos[b].hist is ignored).  Limits: dim = 2, EP_MIXED, n_b <= 8192.  offsets: host array of nprob+1
  * int64 with offsets[0] = 0, non-decreasing.  All problems must share dim.
  * Synchronises the stream.  Returns EP_OK when every problem converged, else
  * the first non-OK status in problem order. */

@@ -486,6 +486,14 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         if (info->h <= 0.0) info->h = 1.0;
         return EP_OK;
     }
+    // small 2-D mixed problems: the whole feedback loop on one CTA (no grid-wide sync per stage)
+    if (P.precision == EP_MIXED && P.dim == 2 && !use_celllist(P, n) && n <= kSmallMatchMaxN) {
+        ep_status s = match_small(params, n, X, Y, p0, info, stream);
+        if (s == EP_ENOTCONVERGED)
+            set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", info->iters, info->resid_inf, info->eps);
+        if (s == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", info->iters);
+        return s;
+    }
     const bool hist_dev = info->hist && is_device_ptr(info->hist);
     Sizer z;
     z.add(forward_bytes(P, n));

@@ -15,7 +15,7 @@
 //     others in its cluster.
 // Each solve runs the whole feedback loop on the GPU: the shoot (RK4 stages
 // with the pair sums over all sources in shared memory, FP32 pair terms,
-// per-particle sums folded into FP64 every kFold sources), the FP64 max-norm
+// per-particle sums over runs of kFold sources added in FP64 when there are several), the FP64 max-norm
 // residual, the FP64 momentum update, and finally H(X, p0) (Eq. H).
 //
 // Scaled coordinates as in the all-pairs path: q' = s (q - c0), c0 the centre of
@@ -53,6 +53,7 @@ struct BProb {
     double eps;
     double s;        // coordinate scale
     double dp_scale;
+    double* hist;    // optional device array (maxit + 1): residual of every shoot
 };
 
 struct BOut {
@@ -150,39 +151,67 @@ __device__ double team_reduce(const Team& t, double v, bool take_max, double* s_
     return r;
 }
 
-// Pair sums over all n sources in shared memory for the thread's particles
-// (slice [lo, hi), stride kThreads); k = (dq, dp) per particle.
-__device__ void pair_sums(const float4* rec, int n, int lo, int hi, int ker, float dp_scale, float (&kq)[kMaxPerThread][2],
-                          float (&kp)[kMaxPerThread][2])
+// Particle of slot r of this thread: L lanes (a power of two dividing 32) share one
+// particle when the slice is small, each summing every L-th source.
+__device__ __forceinline__ int slot_particle(int lo, int L, int r)
 {
+    return lo + (int)threadIdx.x / L + r * (kThreads / L);
+}
+
+// Pair sums over all n sources in shared memory for the thread's particles
+// (slot r: particle slot_particle(lo, L, r) if < hi); k = (dq, dp) per particle,
+// complete in every lane of the particle's lane group.
+__device__ void pair_sums(const float4* rec, int n, int lo, int hi, int L, int ker, float dp_scale,
+                          float (&kq)[kMaxPerThread][2], float (&kp)[kMaxPerThread][2])
+{
+    const int sub = (int)threadIdx.x % L;
 #pragma unroll
     for (int r = 0; r < kMaxPerThread; ++r) {
-        const int i = lo + threadIdx.x + r * kThreads;
+        const int i = slot_particle(lo, L, r);
         kq[r][0] = kq[r][1] = kp[r][0] = kp[r][1] = 0.f;
-        if (i >= hi) continue;
-        const float4 ri = rec[i];
+        if (r > 0 && L > 1) continue;     // lane groups hold one particle each
+        const bool on = i < hi;
+        // FP32 partial sums per run of kFold sources; runs are added in FP64 only when
+        // there is more than one (FP64 costs ~60 FP32 issue slots per warp here)
+        const bool multi = n > kFold;
+        float q0 = 0.f, q1 = 0.f, p0 = 0.f, p1 = 0.f;
         double aq0 = 0, aq1 = 0, ap0 = 0, ap1 = 0;
-        for (int j0 = 0; j0 < n; j0 += kFold) {
-            const int j1 = min(n, j0 + kFold);
-            float q0 = 0.f, q1 = 0.f, p0 = 0.f, p1 = 0.f;
-            for (int j = j0; j < j1; ++j) {
-                const float4 rj = rec[j];
-                const float dx = ri.x - rj.x, dy = ri.y - rj.y;
-                const float r2 = fmaf(dx, dx, dy * dy);
-                float G, w;
-                kfun(ker, r2, G, w);
-                q0 = fmaf(G, rj.z, q0);
-                q1 = fmaf(G, rj.w, q1);
-                const float c = w * fmaf(ri.z, rj.z, ri.w * rj.w);
-                p0 = fmaf(c, dx, p0);
-                p1 = fmaf(c, dy, p1);
+        if (on) {
+            const float4 ri = rec[i];
+            for (int j0 = 0; j0 < n; j0 += kFold) {
+                const int j1 = min(n, j0 + kFold);
+                for (int j = j0 + sub; j < j1; j += L) {
+                    const float4 rj = rec[j];
+                    const float dx = ri.x - rj.x, dy = ri.y - rj.y;
+                    const float r2 = fmaf(dx, dx, dy * dy);
+                    float G, w;
+                    kfun(ker, r2, G, w);
+                    q0 = fmaf(G, rj.z, q0);
+                    q1 = fmaf(G, rj.w, q1);
+                    const float c = w * fmaf(ri.z, rj.z, ri.w * rj.w);
+                    p0 = fmaf(c, dx, p0);
+                    p1 = fmaf(c, dy, p1);
+                }
+                if (multi) {
+                    aq0 += q0; aq1 += q1; ap0 += p0; ap1 += p1;
+                    q0 = q1 = p0 = p1 = 0.f;
+                }
             }
-            aq0 += q0; aq1 += q1; ap0 += p0; ap1 += p1;
         }
-        kq[r][0] = (float)aq0;
-        kq[r][1] = (float)aq1;
-        kp[r][0] = dp_scale * (float)ap0;
-        kp[r][1] = dp_scale * (float)ap1;
+        if (multi) {
+            q0 = (float)aq0; q1 = (float)aq1; p0 = (float)ap0; p1 = (float)ap1;
+        }
+        // combine the lane group in FP32 (whole groups are active or inactive together)
+        for (int o = L >> 1; o > 0; o >>= 1) {
+            q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+            q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+        }
+        kq[r][0] = q0;
+        kq[r][1] = q1;
+        kp[r][0] = dp_scale * p0;
+        kp[r][1] = dp_scale * p1;
     }
 }
 
@@ -206,9 +235,18 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
     const double* X = a.X + 2 * P.off;
     const double* Y = a.Y + 2 * P.off;
     double* p0 = a.p0 + 2 * P.off;
+    // a solo problem keeps its step state and RK4 accumulator in shared memory after
+    // the records (n <= 2047: 16 + 16 + 32 bytes per particle fit the 128 KB region)
     double* xs = a.xs + 4 * P.off;
     float* acc = a.acc + 4 * P.off;
+    if (!t.cluster && n <= kThreads * kMaxPerThread) {
+        acc = reinterpret_cast<float*>(rec + n);
+        xs = reinterpret_cast<double*>(acc + 4 * (size_t)n);
+    }
     const float s_f = (float)P.s, dps = (float)P.dp_scale;
+    int L = 1;
+    while (L < 32 && (hi - lo) * 2 * L <= kThreads) L *= 2;
+    const bool lead = ((int)threadIdx.x % L) == 0;  // the lane that finishes its particle
 
     // centre of the bounding box of X (every CTA computes it)
     double c0x, c0y;
@@ -234,17 +272,13 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
         for (int i = threadIdx.x; i < n; i += kThreads)
             rec[i] = make_float4((float)((X[2 * i] - c0x) * P.s), (float)((X[2 * i + 1] - c0y) * P.s), 1.0f, 0.0f);
         __syncthreads();
-        pair_sums(rec, n, lo, hi, P.kernel, dps, kq, kp);
+        pair_sums(rec, n, lo, hi, L, P.kernel, dps, kq, kp);
         double mx = 0.0;
 #pragma unroll
         for (int r = 0; r < kMaxPerThread; ++r)
-            if (lo + (int)threadIdx.x + r * kThreads < hi) mx = fmax(mx, fabs((double)kq[r][0]));
+            if (slot_particle(lo, L, r) < hi) mx = fmax(mx, fabs((double)kq[r][0]));
         mx = team_reduce(t, mx, true, s_red, s_slot);
         h = mx > 0.0 ? 1.0 / mx : 1.0;
-    }
-    for (int i = lo + threadIdx.x; i < hi; i += kThreads) {
-        p0[2 * i] = 0.0;
-        p0[2 * i + 1] = 0.0;
     }
     team_sync(t);
 
@@ -267,17 +301,17 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
         float4 xr[kMaxPerThread];  // the thread's particles at the start of the step (scaled)
 #pragma unroll
         for (int r = 0; r < kMaxPerThread; ++r) {
-            const int i = lo + threadIdx.x + r * kThreads;
+            const int i = slot_particle(lo, L, r);
             xr[r] = i < hi ? rec[i] : make_float4(0, 0, 0, 0);
         }
         for (int step = 0; step < P.steps; ++step) {
             for (int stage = 0; stage < 4; ++stage) {
-                pair_sums(rec, n, lo, hi, P.kernel, dps, kq, kp);
+                pair_sums(rec, n, lo, hi, L, P.kernel, dps, kq, kp);
                 team_sync(t);  // every CTA has finished reading the stage records
 #pragma unroll
                 for (int r = 0; r < kMaxPerThread; ++r) {
-                    const int i = lo + threadIdx.x + r * kThreads;
-                    if (i >= hi) continue;
+                    const int i = slot_particle(lo, L, r);
+                    if (i >= hi || !lead || (r > 0 && L > 1)) continue;
                     float* A = acc + 4 * i;
                     float4 y;
                     if (stage < 3) {
@@ -318,6 +352,7 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
         bad = team_reduce(t, bad, true, s_red, s_slot);
         mx = team_reduce(t, mx, true, s_red, s_slot);
         res = bad > 0.0 ? NAN : mx;
+        if (P.hist && t.rank == 0 && threadIdx.x == 0) P.hist[k] = res;
         if (bad > 0.0) { status = EP_EDIVERGED; break; }
         if (res < P.eps) { status = EP_OK; break; }
         if (k == P.maxit) { status = EP_ENOTCONVERGED; break; }
@@ -333,12 +368,13 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
         rec[i] = make_float4((float)((X[2 * i] - c0x) * P.s), (float)((X[2 * i + 1] - c0y) * P.s),
                              (float)__ldcg(p0 + 2 * i), (float)__ldcg(p0 + 2 * i + 1));
     __syncthreads();
-    pair_sums(rec, n, lo, hi, P.kernel, dps, kq, kp);
+    pair_sums(rec, n, lo, hi, L, P.kernel, dps, kq, kp);
     double hs = 0.0;
 #pragma unroll
     for (int r = 0; r < kMaxPerThread; ++r) {
-        const int i = lo + threadIdx.x + r * kThreads;
-        if (i < hi) hs += 0.5 * (p0[2 * i] * (double)kq[r][0] + p0[2 * i + 1] * (double)kq[r][1]);
+        const int i = slot_particle(lo, L, r);
+        if (i < hi && lead && !(r > 0 && L > 1))
+            hs += 0.5 * (__ldcg(p0 + 2 * i) * (double)kq[r][0] + __ldcg(p0 + 2 * i + 1) * (double)kq[r][1]);
     }
     hs = team_reduce(t, hs, false, s_red, s_slot);
     if (t.rank == 0 && threadIdx.x == 0) {
@@ -395,8 +431,44 @@ bool is_dev(const void* p)
 
 }  // namespace
 
+ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets, const double* X, const double* Y,
+                      double* p0, ep_match_info* infos, void* stream, double* const* hist_dev);
+
+
 ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offsets, const double* X,
                         const double* Y, double* p0, ep_match_info* infos, void* stream)
+{
+    return batched_run(params, nprob, offsets, X, Y, p0, infos, stream, nullptr);
+}
+
+// ep_match of one small 2-D mixed-precision problem on one CTA (the batched solver).
+ep_status match_small(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
+                      ep_match_info* info, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t offsets[2] = {0, n};
+    double* hdev = nullptr;
+    bool hist_host = false;
+    if (info->hist) {
+        if (is_dev(info->hist)) {
+            hdev = info->hist;
+        } else {
+            hist_host = true;
+            EP_TRY_CUDA(cudaMallocAsync(&hdev, sizeof(double) * (info->maxit + 1), st));
+        }
+    }
+    ep_status s = batched_run(params, 1, offsets, X, Y, p0, info, stream, &hdev);
+    if (hist_host) {
+        EP_TRY_CUDA(cudaMemcpyAsync(info->hist, hdev, sizeof(double) * (info->iters + 1), cudaMemcpyDeviceToHost, st));
+        EP_TRY_CUDA(cudaFreeAsync(hdev, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    return s;
+}
+
+
+ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets, const double* X, const double* Y,
+                      double* p0, ep_match_info* infos, void* stream, double* const* hist_dev)
 {
     if (nprob < 0) return set_error("ep_match_batched: nprob < 0"), EP_EINVAL;
     if (nprob == 0) return EP_OK;
@@ -431,6 +503,7 @@ ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offse
         q.eps = I.eps;
         q.s = ks.s;
         q.dp_scale = ks.dp_scale;
+        q.hist = hist_dev ? hist_dev[b] : nullptr;
     }
     const int64_t ntot = offsets[nprob];
     // order: team problems then solo problems, each by decreasing n^2 (LPT)
@@ -474,8 +547,11 @@ ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offse
         EP_TRY_CUDA(cudaMemcpyAsync(t, Y, sizeof(double) * m, cudaMemcpyHostToDevice, st));
         dY = t;
     }
-    if (ph) dp0 = (double*)ar->carve(sizeof(double) * m + 8);
-    if (!dp0) return set_error("ep_match_batched: workspace too small"), EP_ENOMEM;
+    if (ph) {
+        dp0 = (double*)ar->carve(sizeof(double) * m + 8);
+        if (!dp0) return set_error("ep_match_batched: workspace too small"), EP_ENOMEM;
+        EP_TRY_CUDA(cudaMemcpyAsync(dp0, p0, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    }
     EP_TRY_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, st));
     EP_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
     EP_TRY_CUDA(cudaMemsetAsync(dctr, 0, sizeof(int) * 4, st));
@@ -537,5 +613,6 @@ ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offse
     if (first != EP_OK) set_error("ep_match_batched: not every problem converged");
     return first;
 }
+
 
 }  // namespace ep
