@@ -132,6 +132,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def aggregate(ms: float, work: float, dist=None, device=None):
+    """Whole-job numbers over the ranks: the slowest rank's time and the sum of the
+    work (pair interactions) every rank did.  Returns (max_ms, total_work)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, work
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def pairs_of(n: int, steps: int, shoots: int) -> int:
     # 4 RHS per RK4 step per shoot, + the default-gain RHS + the final-H RHS
     return n * n * (4 * steps * shoots + 2)
@@ -192,15 +206,7 @@ def run_gb300(args):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     clk = clocks.stop()
     local_pairs = n * n * (4 * S * shoots + 2 * args.steps)
-    t_max = ms
-    total_pairs = local_pairs
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([float(local_pairs)], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        total_pairs = float(c.item())
+    t_max, total_pairs = aggregate(ms, local_pairs, dist, dev)
     value = total_pairs / (t_max / 1e3)
 
     # ---- dominant kernel: the persistent shoot (one cooperative launch per shoot,

@@ -23,7 +23,11 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -554,8 +558,6 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     }
     EP_TRY_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, st));
     EP_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
-    EP_TRY_CUDA(cudaMemsetAsync(dctr, 0, sizeof(int) * 4, st));
-
     BArgs a{};
     a.probs = dprobs;
     a.outs = douts;
@@ -571,11 +573,10 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
 
     // persistent grid: as many clusters as can be resident at once
     const size_t smem = sizeof(float4) * kMaxN;
-    static bool attr = false;
-    if (!attr) {
-        EP_TRY_CUDA(cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::mutex mu;
+    static std::map<int, int> resident;  // device -> resident clusters
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attrs[1];
     attrs[0].id = cudaLaunchAttributeClusterDimension;
@@ -584,18 +585,59 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     attrs[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
     cfg.attrs = attrs;
     cfg.numAttrs = 1;
-    DeviceInfo di{};
-    EP_TRY(device_info(&di));
-    cfg.gridDim = dim3((unsigned)(di.sm_count / kCluster * kCluster));
     int nclusters = 0;
-    EP_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_batched, &cfg));
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = resident.find(di.device);
+        if (it == resident.end()) {
+            EP_TRY_CUDA(cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            cfg.gridDim = dim3((unsigned)(di.sm_count / kCluster * kCluster));
+            EP_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_batched, &cfg));
+            resident[di.device] = nclusters;
+        } else {
+            nclusters = it->second;
+        }
+    }
     if (nclusters < 1) return set_error("ep_match_batched: no cluster of %d CTAs fits", kCluster), EP_ECUDA;
     cfg.gridDim = dim3((unsigned)(nclusters * kCluster));
-    count_launch();
-    EP_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_batched, a));
+
+    // The launch (counter reset + persistent kernel) is a CUDA graph, captured on a
+    // library stream and replayed on the caller's stream; it is rebuilt only when
+    // the kernel arguments change (new buffers or sizes).
+    struct GraphCache {
+        cudaStream_t cap = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        BArgs args{};
+        unsigned grid = 0;
+    };
+    static std::map<std::pair<int, cudaStream_t>, GraphCache> graphs;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        GraphCache& gc = graphs[{di.device, st}];
+        if (!gc.exec || memcmp(&gc.args, &a, sizeof a) != 0 || gc.grid != cfg.gridDim.x) {
+            if (gc.exec) {
+                EP_TRY_CUDA(cudaStreamSynchronize(st));
+                cudaGraphExecDestroy(gc.exec);
+                gc.exec = nullptr;
+            }
+            if (!gc.cap) EP_TRY_CUDA(cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            EP_TRY_CUDA(cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal));
+            cudaMemsetAsync(dctr, 0, sizeof(int) * 4, gc.cap);
+            cfg.stream = gc.cap;
+            cudaLaunchKernelEx(&cfg, k_batched, a);
+            EP_TRY_CUDA(cudaStreamEndCapture(gc.cap, &graph));
+            cudaError_t e = cudaGraphInstantiate(&gc.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batched launch)");
+            gc.args = a;
+            gc.grid = cfg.gridDim.x;
+        }
+        count_launch();
+        EP_TRY_CUDA(cudaGraphLaunch(gc.exec, st));
+    }
 
     std::vector<BOut> outs((size_t)nprob);
     EP_TRY_CUDA(cudaMemcpyAsync(outs.data(), douts, sizeof(BOut) * nprob, cudaMemcpyDeviceToHost, st));
