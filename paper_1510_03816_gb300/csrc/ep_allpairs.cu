@@ -378,8 +378,8 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 //   G_ij = 2^-|q''_i|^2 * 2^t,   t = 2 q''_i . q''_j - |q''_j|^2  (<= |q''_i|^2),
 //   dq_i = E_i sum_j g_ij p_j,   M_i = q''_i (x) dq_i - E_i sum_j g_ij (q''_j (x) p_j),
 // with g = 2^t and E_i = 2^-|q''_i|^2, so a pair costs two FMAs for t, one ex2 and
-// six FMAs, against per-source records (2x, 2y, -|q''|^2, px), (py, x px, x py,
-// y px), (y py) built once per staged chunk.  t never exceeds |q''_i|^2; a tile
+// three packed f32x2 FMAs (six FP32 FMAs), against per-source records
+// (2x, 2y, -|q''|^2, y px), (px, py, x px, x py), (y py) built once per staged chunk.  t never exceeds |q''_i|^2; a tile
 // whose |q''_i|^2 could overflow (> kFactorMax) takes the difference form
 // d = q''_i - q''_j instead (same records).
 constexpr int kTileG = 128;
@@ -430,20 +430,19 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
             mq = fmaxf(mq, fmaf(qx[r], qx[r], qy[r] * qy[r]));
         }
         const bool factored = !__syncthreads_or(mq > kFactorMax);
-        float sq0[RI], sq1[RI], sb[RI][4];
+        // per particle: (sum g px, sum g py), (sum g x px, sum g x py), (sum g y px, sum g y py),
+        // packed so every accumulation is one f32x2 FMA
+        float2 sqv[RI], sbx[RI], sby[RI];
 #pragma unroll
-        for (int r = 0; r < RI; ++r) {
-            sq0[r] = sq1[r] = 0.0f;
-            sb[r][0] = sb[r][1] = sb[r][2] = sb[r][3] = 0.0f;
-        }
+        for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
         for (int cj = j0; cj < j1; cj += kChunkG) {
             const int L = min(kChunkG, j1 - cj);
             __syncthreads();
             for (int t = threadIdx.x; t < L; t += THREADS) {
                 const float4 v = cj == j0 ? pre[t / THREADS] : __ldcg(a.S_in + cj + t);
                 const float x = v.x - c4.x, y = v.y - c4.y;
-                recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), v.z);
-                recA[2 * t + 1] = make_float4(v.w, x * v.z, x * v.w, y * v.z);
+                recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), y * v.z);
+                recA[2 * t + 1] = make_float4(v.z, v.w, x * v.z, x * v.w);
                 recB[t] = y * v.w;
             }
             __syncthreads();
@@ -451,17 +450,18 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
             if (factored) {
 #pragma unroll 2
                 for (int j = ja; j < jb; ++j) {
+                    // A = (2x, 2y, -|q''|^2, y px), B = (px, py, x px, x py), byy = y py
                     const float4 A = recA[2 * j], B = recA[2 * j + 1];
                     const float byy = recB[j];
+                    const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
+                    const float2 yp = make_float2(A.w, byy);
 #pragma unroll
                     for (int r = 0; r < RI; ++r) {
                         const float g = ex2_approx(fmaf(qx[r], A.x, fmaf(qy[r], A.y, A.z)));
-                        sq0[r] = fmaf(g, A.w, sq0[r]);
-                        sq1[r] = fmaf(g, B.x, sq1[r]);
-                        sb[r][0] = fmaf(g, B.y, sb[r][0]);
-                        sb[r][1] = fmaf(g, B.z, sb[r][1]);
-                        sb[r][2] = fmaf(g, B.w, sb[r][2]);
-                        sb[r][3] = fmaf(g, byy, sb[r][3]);
+                        const float2 gg = make_float2(g, g);
+                        sqv[r] = __ffma2_rn(gg, pxy, sqv[r]);
+                        sbx[r] = __ffma2_rn(gg, xp, sbx[r]);
+                        sby[r] = __ffma2_rn(gg, yp, sby[r]);
                     }
                 }
             } else {
@@ -469,16 +469,16 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
                 for (int j = ja; j < jb; ++j) {
                     const float4 A = recA[2 * j], B = recA[2 * j + 1];
                     const float byy = recB[j];
+                    const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
+                    const float2 yp = make_float2(A.w, byy);
 #pragma unroll
                     for (int r = 0; r < RI; ++r) {
                         const float dx = fmaf(-0.5f, A.x, qx[r]), dy = fmaf(-0.5f, A.y, qy[r]);
                         const float G = ex2_approx(-fmaf(dx, dx, dy * dy));
-                        sq0[r] = fmaf(G, A.w, sq0[r]);
-                        sq1[r] = fmaf(G, B.x, sq1[r]);
-                        sb[r][0] = fmaf(G, B.y, sb[r][0]);
-                        sb[r][1] = fmaf(G, B.z, sb[r][1]);
-                        sb[r][2] = fmaf(G, B.w, sb[r][2]);
-                        sb[r][3] = fmaf(G, byy, sb[r][3]);
+                        const float2 gg = make_float2(G, G);
+                        sqv[r] = __ffma2_rn(gg, pxy, sqv[r]);
+                        sbx[r] = __ffma2_rn(gg, xp, sbx[r]);
+                        sby[r] = __ffma2_rn(gg, yp, sby[r]);
                     }
                 }
             }
@@ -489,14 +489,14 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
             const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
-            const float d0 = E * sq0[r], d1 = E * sq1[r];
+            const float d0 = E * sqv[r].x, d1 = E * sqv[r].y;
             float* o = red + (size_t)warp * kKWidth * kTileG + lane + 32 * r;
             o[0 * kTileG] = d0;
             o[1 * kTileG] = d1;
-            o[2 * kTileG] = fmaf(qx[r], d0, -E * sb[r][0]);
-            o[3 * kTileG] = fmaf(qx[r], d1, -E * sb[r][1]);
-            o[4 * kTileG] = fmaf(qy[r], d0, -E * sb[r][2]);
-            o[5 * kTileG] = fmaf(qy[r], d1, -E * sb[r][3]);
+            o[2 * kTileG] = fmaf(qx[r], d0, -E * sbx[r].x);
+            o[3 * kTileG] = fmaf(qx[r], d1, -E * sbx[r].y);
+            o[4 * kTileG] = fmaf(qy[r], d0, -E * sby[r].x);
+            o[5 * kTileG] = fmaf(qy[r], d1, -E * sby[r].y);
         }
         __syncthreads();
         for (int t = threadIdx.x; t < kKWidth * kTileG; t += THREADS) {
