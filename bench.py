@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only run warmup + steps shoots of the workload (for ncu captures); no JSON line")
+    ap.add_argument("--profile-rk4-steps", type=int, default=0,
+                    help="with --profile: RK4 steps per shoot (0 = the workload's 100), for short captures")
     return ap.parse_args()
 
 
@@ -174,8 +176,12 @@ def run_gb300(args):
 
     if args.profile:
         p0 = 0.002 * (Y - X)
+        pprm = prm
+        if args.profile_rk4_steps > 0:
+            pprm = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=args.profile_rk4_steps,
+                             precision=ep.MIXED, neigh=ep.ALLPAIRS)
         for _ in range(args.warmup + args.steps):
-            ep.shoot(X, p0, prm)
+            ep.shoot(X, p0, pprm)
         torch.cuda.synchronize()
         return
 

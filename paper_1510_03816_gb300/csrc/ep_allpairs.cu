@@ -26,7 +26,7 @@
 #include <mutex>
 #include <vector>
 
-#include "ep_allpairs.cuh"
+#include "ep_allpairs_dev.cuh"
 
 namespace ep {
 
@@ -35,213 +35,6 @@ namespace {
 constexpr int kChunk = 2048;  // sources staged per shared-memory fill (mixed)
 constexpr int kChunk64 = 1024;
 
-struct StageArgs {
-    long long U;
-    int n;
-    int G;
-    int mode;
-    int stage;
-    float dt_f;
-    double dt;
-    float s_f;
-    double s;
-    double dp_scale;
-    float dp_scale_f;
-    const double* c0;
-    const float4* S_in;
-    float4* S_out;
-    const float4* Sx;   // step-start stage copy (mixed)
-    float4* Sx_w;       // written at stage 3 (mixed)
-    const double* D_in; // fp64 stage copies
-    double* D_out;
-    double* x;
-    float* acc;
-    double* dacc;
-    double* K;
-    int* counters;
-    double* out_q;
-    double* out_p;
-};
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Kernel value G and momentum weight w of one pair from the scaled squared
-// distance r2 = |d'|^2 (see ep_common.cuh for the scalings).
-template <int KER>
-__device__ __forceinline__ void kfun_f32(float r2, float& G, float& w)
-{
-    if constexpr (KER == EP_GAUSS) {
-        G = ex2_approx(-r2);
-        w = G;
-    } else if constexpr (KER == EP_TENT) {
-        // r2 = 0 (self or coincident pair): rs stays finite and d' = 0, so the
-        // momentum term vanishes (phi = 0 at r = 0) while G(0) = 1.
-        const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
-        const bool in = r2 < 1.0f;
-        G = in ? fmaf(-r2, rs, 1.0f) : 0.0f;
-        w = in ? rs : 0.0f;
-    } else {
-        const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
-        G = ex2_approx(-r2 * rs);
-        w = G * rs;
-    }
-}
-
-// Exact FP64 kernel value and phi = G'(r)/r (unscaled).
-template <int KER>
-__device__ __forceinline__ void kfun_f64(double r2, double sigma, double& G, double& phi)
-{
-    if constexpr (KER == EP_GAUSS) {
-        G = exp(-r2 / (2.0 * sigma * sigma));
-        phi = -G / (sigma * sigma);
-    } else if constexpr (KER == EP_TENT) {
-        const double r = sqrt(r2);
-        const bool in = r < sigma;
-        G = in ? 1.0 - r / sigma : 0.0;
-        phi = (in && r > 0.0) ? -1.0 / (sigma * r) : 0.0;
-    } else {
-        const double r = sqrt(r2);
-        G = exp(-r / sigma);
-        phi = r > 0.0 ? -G / (sigma * r) : 0.0;
-    }
-}
-
-__device__ __forceinline__ int cta_of_unit(long long u, long long U, int G)
-{
-    return (int)(((u + 1) * (long long)G - 1) / U);
-}
-
-__device__ __forceinline__ int tile_contributors(int b, const StageArgs& a)
-{
-    const long long ub = (long long)b * a.n;
-    return cta_of_unit(ub + a.n - 1, a.U, a.G) - cta_of_unit(ub, a.U, a.G) + 1;
-}
-
-// ------------------------------------------------------------------ mixed
-// Epilogue of one particle i in tile order; k = (dq, dp) of the stage input.
-template <int DIM>
-__device__ void epilogue_mixed(const StageArgs& a, int i)
-{
-    constexpr int V = DIM == 2 ? 1 : 2;
-    double kk[kKWidth];
-#pragma unroll
-    for (int t = 0; t < kKWidth; ++t) {
-        kk[t] = __ldcg(a.K + (size_t)i * kKWidth + t);
-        a.K[(size_t)i * kKWidth + t] = 0.0;
-    }
-    // momentum of the stage input (FP32 copy) for the 2-D contraction
-    float pin[3];
-    if constexpr (DIM == 2) {
-        const float4 v = __ldcg(a.S_in + i);
-        pin[0] = v.z;
-        pin[1] = v.w;
-    } else {
-        const float4 v = __ldcg(a.S_in + 2 * (size_t)i + 1);
-        pin[0] = v.x;
-        pin[1] = v.y;
-        pin[2] = v.z;
-    }
-    if (a.mode == MODE_RHS) {
-        double kq[DIM], kp[DIM];
-        if constexpr (DIM == 2) {
-            kq[0] = kk[0];
-            kq[1] = kk[1];
-            kp[0] = a.dp_scale * (kk[2] * (double)pin[0] + kk[3] * (double)pin[1]);
-            kp[1] = a.dp_scale * (kk[4] * (double)pin[0] + kk[5] * (double)pin[1]);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                kq[c] = kk[c];
-                kp[c] = a.dp_scale * kk[3 + c];
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-            a.out_q[(size_t)i * DIM + c] = kq[c];
-            a.out_p[(size_t)i * DIM + c] = kp[c];
-        }
-        return;
-    }
-    float kq[DIM], kp[DIM];
-    if constexpr (DIM == 2) {
-        kq[0] = (float)kk[0];
-        kq[1] = (float)kk[1];
-        kp[0] = a.dp_scale_f * fmaf((float)kk[2], pin[0], (float)kk[3] * pin[1]);
-        kp[1] = a.dp_scale_f * fmaf((float)kk[4], pin[0], (float)kk[5] * pin[1]);
-    } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            kq[c] = (float)kk[c];
-            kp[c] = a.dp_scale_f * (float)kk[3 + c];
-        }
-    }
-    float* A = a.acc + (size_t)i * 2 * DIM;
-    if (a.stage < 3) {
-        // y_{s+1} = x_n + c_{s+1} dt k_s, c = 1/2, 1/2, 1 (FP32, scaled positions)
-        const float cdt = (a.stage == 2 ? 1.0f : 0.5f) * a.dt_f;
-        const float bw = a.stage == 0 ? 1.0f : 2.0f;
-        float xs[2 * DIM];
-        if constexpr (DIM == 2) {
-            const float4 v = a.Sx[i];
-            xs[0] = v.x; xs[1] = v.y; xs[2] = v.z; xs[3] = v.w;
-        } else {
-            const float4 v0 = a.Sx[2 * (size_t)i], v1 = a.Sx[2 * (size_t)i + 1];
-            xs[0] = v0.x; xs[1] = v0.y; xs[2] = v0.z; xs[3] = v1.x; xs[4] = v1.y; xs[5] = v1.z;
-        }
-        float y[2 * DIM];
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-            y[c] = fmaf(cdt * a.s_f, kq[c], xs[c]);
-            y[DIM + c] = fmaf(cdt, kp[c], xs[DIM + c]);
-            if (a.stage == 0) {
-                A[c] = kq[c];
-                A[DIM + c] = kp[c];
-            } else {
-                A[c] = fmaf(bw, kq[c], A[c]);
-                A[DIM + c] = fmaf(bw, kp[c], A[DIM + c]);
-            }
-        }
-        if constexpr (DIM == 2) {
-            a.S_out[i] = make_float4(y[0], y[1], y[2], y[3]);
-        } else {
-            a.S_out[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
-            a.S_out[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
-        }
-    } else {
-        // x_{n+1} = x_n + dt/6 (k1 + 2 k2 + 2 k3 + k4): the increment in FP32, the state in FP64
-        const int n = a.n;
-        double* xq = a.x + (size_t)i * DIM;
-        double* xp = a.x + (size_t)n * DIM + (size_t)i * DIM;
-        float y[2 * DIM];
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-            const double nq = xq[c] + (double)(a.dt_f * (1.0f / 6.0f) * (A[c] + kq[c]));
-            const double np = xp[c] + (double)(a.dt_f * (1.0f / 6.0f) * (A[DIM + c] + kp[c]));
-            xq[c] = nq;
-            xp[c] = np;
-            y[c] = (float)((nq - a.c0[c]) * a.s);
-            y[DIM + c] = (float)np;
-        }
-        if constexpr (DIM == 2) {
-            a.Sx_w[i] = make_float4(y[0], y[1], y[2], y[3]);
-        } else {
-            a.Sx_w[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
-            a.Sx_w[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
-        }
-    }
-}
 
 // The pair phase of one stage over this CTA's stream-K range: per tile segment,
 // stage the sources in shared memory, sum in registers, reduce over warps and
@@ -371,7 +164,205 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
     }
 }
 
-// ------------------------------------------------------------------ 2-D Gaussian, factored
+// ------------------------------------------------------------------ 2-D Gaussian, owner computes
+// The persistent 2-D Gaussian shoot splits the particles, not the pair matrix: CTA c
+// owns rows [c n / G, (c+1) n / G) and sums over every source j itself, so a stage
+// needs no cross-CTA reduction: the CTA applies the RK4 stage to its own rows and
+// one grid-wide barrier per stage publishes the next stage's inputs.
+//
+// Rows are processed in sub-tiles of R = (32 / JL) x 4 particles.  A warp's lanes
+// are (32 / JL) row groups x JL source lanes; a lane holds 4 rows (row group g:
+// rows g, g + 32/JL, ...) and takes every JL-th source of its warp's share, so each
+// staged source record feeds 4 particles of the lane.  The source lanes and the
+// warps are reduced after the sub-tile (shuffles, then shared memory).
+//
+// Factored Gaussian on coordinates centred on the sub-tile's first particle,
+// q'' = q' - q'_first: with G = 2^-|q''_i - q''_j|^2 (scaled units),
+//   G_ij = E_i g_ij,  E_i = 2^-|q''_i|^2,  g_ij = 2^t,  t = 2 q''_i . q''_j - |q''_j|^2 (<= |q''_i|^2),
+//   dq_i = E_i sum_j g_ij p_j,   M_i = q''_i (x) dq_i - E_i sum_j g_ij (q''_j (x) p_j),
+// so a pair costs two FMAs for t, one ex2 and three packed f32x2 FMAs, against
+// per-source records (2x, 2y, -|q''|^2, y px), (px, py, x px, x py), (y py) built
+// once per staged chunk.  A sub-tile whose |q''_i|^2 could overflow 2^t
+// (> kFactorMax) takes the difference form d = q''_i - q''_j (same records).
+constexpr int kChunkG = 2048;
+constexpr float kFactorMax = 60.0f;
+
+// RK4 stage of component comp (0, 1: q; 2, 3: p) of particle i from its six FP32
+// pair sums f (dq_x, dq_y, M_xx, M_xy, M_yx, M_yy): the 2-D mixed epilogue with
+// one thread per component.  Only the step update (stage 3) touches FP64.
+__device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int comp, const float* f)
+{
+    float kv;
+    if (comp < 2) {
+        kv = comp == 0 ? f[0] : f[1];
+    } else {
+        const float2 pin = __ldcg(reinterpret_cast<const float2*>(a.S_in + i) + 1);
+        const float m0 = comp == 2 ? f[2] : f[4], m1 = comp == 2 ? f[3] : f[5];
+        kv = a.dp_scale_f * fmaf(m0, pin.x, m1 * pin.y);
+    }
+    if (a.mode == MODE_RHS) {
+        double* out = comp < 2 ? a.out_q : a.out_p;
+        out[(size_t)i * 2 + (comp & 1)] = (double)kv;
+        return;
+    }
+    float* A = a.acc + (size_t)i * 4 + comp;
+    if (a.stage < 3) {
+        const float cdt = (a.stage == 2 ? 1.0f : 0.5f) * a.dt_f;
+        const float xs = reinterpret_cast<const float*>(a.Sx + i)[comp];
+        const float y = fmaf(comp < 2 ? cdt * a.s_f : cdt, kv, xs);
+        *A = a.stage == 0 ? kv : fmaf(2.0f, kv, *A);  // k1 + 2 k2 + 2 k3
+        reinterpret_cast<float*>(a.S_out + i)[comp] = y;
+    } else {
+        const int n = a.n;
+        double* xv = comp < 2 ? a.x + (size_t)i * 2 + comp : a.x + (size_t)n * 2 + (size_t)i * 2 + (comp - 2);
+        const double nv = *xv + (double)(a.dt_f * (1.0f / 6.0f) * (*A + kv));
+        *xv = nv;
+        reinterpret_cast<float*>(a.Sx_w + i)[comp] = comp < 2 ? (float)((nv - a.c0[comp]) * a.s) : (float)nv;
+    }
+}
+
+template <int THREADS, int JL>
+__device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* smem, int r0, int r1)
+{
+    constexpr int W = THREADS / 32;
+    constexpr int RI = 4;
+    constexpr int RG = 32 / JL;  // row groups per warp
+    constexpr int R = RG * RI;   // rows per sub-tile
+    float4* recA = smem;                                         // [2 * kChunkG]
+    float* recB = reinterpret_cast<float*>(smem + 2 * kChunkG);  // [kChunkG]
+    float* red = reinterpret_cast<float*>(smem + 2 * kChunkG) + kChunkG;  // [W][6][R], then [6][R]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rg = lane / JL, jl = lane % JL;
+    const int n = a.n;
+    for (int t0 = r0; t0 < r1; t0 += R) {
+        const int t1 = min(r1, t0 + R);
+        constexpr int PF = kChunkG / THREADS;
+        const int L0 = min(kChunkG, n);
+        float4 pre[PF];
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            const int t = threadIdx.x + k * THREADS;
+            pre[k] = t < L0 ? __ldcg(a.S_in + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float4 c4 = __ldcg(a.S_in + t0);  // sub-tile centre: its first particle
+        float qx[RI], qy[RI];
+        float mq = 0.0f;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int i = t0 + rg + RG * r;
+            const float4 v = i < t1 ? __ldcg(a.S_in + i) : c4;
+            qx[r] = v.x - c4.x;
+            qy[r] = v.y - c4.y;
+            mq = fmaxf(mq, fmaf(qx[r], qx[r], qy[r] * qy[r]));
+        }
+        const bool factored = !__syncthreads_or(mq > kFactorMax);
+        float2 sqv[RI], sbx[RI], sby[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
+        for (int cj = 0; cj < n; cj += kChunkG) {
+            const int L = min(kChunkG, n - cj);
+            __syncthreads();
+            for (int t = threadIdx.x; t < L; t += THREADS) {
+                const float4 v = cj == 0 ? pre[t / THREADS] : __ldcg(a.S_in + cj + t);
+                const float x = v.x - c4.x, y = v.y - c4.y;
+                recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), y * v.z);
+                recA[2 * t + 1] = make_float4(v.z, v.w, x * v.z, x * v.w);
+                recB[t] = y * v.w;
+            }
+            __syncthreads();
+            const int ja = warp * L / W + jl, jb = (warp + 1) * L / W;
+            if (factored) {
+#pragma unroll 2
+                for (int j = ja; j < jb; j += JL) {
+                    // A = (2x, 2y, -|q''|^2, y px), B = (px, py, x px, x py), byy = y py
+                    const float4 A = recA[2 * j], B = recA[2 * j + 1];
+                    const float byy = recB[j];
+                    const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
+                    const float2 yp = make_float2(A.w, byy);
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const float g = ex2_approx(fmaf(qx[r], A.x, fmaf(qy[r], A.y, A.z)));
+                        const float2 gg = make_float2(g, g);
+                        sqv[r] = __ffma2_rn(gg, pxy, sqv[r]);
+                        sbx[r] = __ffma2_rn(gg, xp, sbx[r]);
+                        sby[r] = __ffma2_rn(gg, yp, sby[r]);
+                    }
+                }
+            } else {
+                for (int j = ja; j < jb; j += JL) {
+                    const float4 A = recA[2 * j], B = recA[2 * j + 1];
+                    const float byy = recB[j];
+                    const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
+                    const float2 yp = make_float2(A.w, byy);
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const float dx = fmaf(-0.5f, A.x, qx[r]), dy = fmaf(-0.5f, A.y, qy[r]);
+                        const float G = ex2_approx(-fmaf(dx, dx, dy * dy));
+                        const float2 gg = make_float2(G, G);
+                        sqv[r] = __ffma2_rn(gg, pxy, sqv[r]);
+                        sbx[r] = __ffma2_rn(gg, xp, sbx[r]);
+                        sby[r] = __ffma2_rn(gg, yp, sby[r]);
+                    }
+                }
+            }
+        }
+        // source lanes -> lane jl == 0 of each row group
+#pragma unroll
+        for (int off = 1; off < JL; off <<= 1) {
+#pragma unroll
+            for (int r = 0; r < RI; ++r) {
+                sqv[r].x += __shfl_xor_sync(0xffffffffu, sqv[r].x, off);
+                sqv[r].y += __shfl_xor_sync(0xffffffffu, sqv[r].y, off);
+                sbx[r].x += __shfl_xor_sync(0xffffffffu, sbx[r].x, off);
+                sbx[r].y += __shfl_xor_sync(0xffffffffu, sbx[r].y, off);
+                sby[r].x += __shfl_xor_sync(0xffffffffu, sby[r].x, off);
+                sby[r].y += __shfl_xor_sync(0xffffffffu, sby[r].y, off);
+            }
+        }
+        // per row: dq = E sq, M = q'' (x) dq - E sb (E = 1 in the difference form);
+        // the warps' partials go to shared memory [W][6][R]
+        if (jl == 0) {
+#pragma unroll
+            for (int r = 0; r < RI; ++r) {
+                const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
+                const float d0 = E * sqv[r].x, d1 = E * sqv[r].y;
+                float* o = red + (size_t)warp * kKWidth * R + rg + RG * r;
+                o[0 * R] = d0;
+                o[1 * R] = d1;
+                o[2 * R] = fmaf(qx[r], d0, -E * sbx[r].x);
+                o[3 * R] = fmaf(qx[r], d1, -E * sbx[r].y);
+                o[4 * R] = fmaf(qy[r], d0, -E * sby[r].x);
+                o[5 * R] = fmaf(qy[r], d1, -E * sby[r].y);
+            }
+        }
+        __syncthreads();
+        float* fin = red + (size_t)W * kKWidth * R;  // [6][R]
+        for (int t = threadIdx.x; t < kKWidth * R; t += THREADS) {
+            float sum = 0.0f;
+#pragma unroll 8
+            for (int w2 = 0; w2 < W; ++w2) sum += red[w2 * kKWidth * R + t];
+            fin[t] = sum;
+        }
+        __syncthreads();
+        // the RK4 stage of the sub-tile's rows, one thread per component
+        if (threadIdx.x < 4 * R) {
+            const int rl = threadIdx.x >> 2, comp = threadIdx.x & 3;
+            const int i = t0 + rl;
+            if (i < t1) {
+                float f[kKWidth];
+#pragma unroll
+                for (int k = 0; k < kKWidth; ++k) f[k] = fin[k * R + rl];
+                epilogue2_comp(a, i, comp, f);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ 2-D Gaussian, stream-K
+// The stream-K alternative of the persistent 2-D Gaussian shoot (the tuner picks it
+// for large n, where the owner split would leave lanes or SMs idle): the pair
+// matrix is cut into equal ranges of (tile, source) units, partial sums go to the
+// FP64 accumulator K, and the RK4 stage runs after a grid barrier.
 // The pair phase of the 2-D Gaussian in tiles of kTileG = 128 particles (32 lanes
 // x 4 registers), on coordinates centred on the tile's first particle,
 // q'' = q' - q'_first.  With G = 2^-|q''_i - q''_j|^2 (scaled units),
@@ -383,8 +374,6 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 // whose |q''_i|^2 could overflow (> kFactorMax) takes the difference form
 // d = q''_i - q''_j instead (same records).
 constexpr int kTileG = 128;
-constexpr int kChunkG = 2048;
-constexpr float kFactorMax = 60.0f;
 
 template <int THREADS>
 __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* smem)
@@ -511,6 +500,27 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
     }
 }
 
+// The owner-computes shoot (mode RK4: `steps` steps) or one RHS (mode RHS, input Sx).
+template <int THREADS, int JL>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_shoot_owner(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
+{
+    extern __shared__ float4 smem[];
+    const int n = a.n;
+    const int r0 = (int)((long long)blockIdx.x * n / gridDim.x), r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
+    unsigned epoch = 0;
+    a.Sx = Sx;
+    const int nst = a.mode == MODE_RHS ? 1 : 4 * steps;
+    for (int st = 0; st < nst; ++st) {
+        const int stage = st & 3;
+        a.stage = stage;
+        a.S_in = a.mode == MODE_RHS || stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
+        a.S_out = stage == 1 ? Sb : Sa;
+        stage_owner_gauss2<THREADS, JL>(a, smem, r0, r1);
+        if (st + 1 < nst && !grid_barrier(bar, err, ++epoch)) return;
+    }
+}
+
 template <int DIM, int KER, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
 {
@@ -519,55 +529,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
     stage_pairs<DIM, KER, THREADS, true>(a, smem, &s_last);
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs resident).  The counter
-// only grows: barrier number e completes when it reaches e * gridDim.x.  The
-// wait is bounded; on giving up it raises the shared error flag, and every CTA
-// that sees the flag returns false so the kernel ends instead of hanging.
-constexpr long long kSpinLimit = 1LL << 22;
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ bool grid_barrier(unsigned* bar, int* err, unsigned epoch)
-{
-    // bar[0..7]: arrival counters, CTA c arrives on bar[c % 8] (spreads the atomics
-    // over eight L2 lines); barrier e completes when bar[k] reaches e * (CTAs on k)
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        const unsigned G = gridDim.x;
-        if (lane == 0) {
-            __threadfence();
-            atomicAdd(bar + (blockIdx.x & 7), 1u);
-        }
-        const unsigned mine = lane < 8 ? (G / 8 + ((unsigned)lane < (G & 7) ? 1u : 0u)) : 0u;
-        const unsigned target = epoch * mine;
-        int ok = 1;
-        long long spins = 0;
-        for (;;) {
-            const unsigned v = lane < 8 ? ld_acquire_u32(bar + lane) : 0u;
-            if (__all_sync(0xffffffffu, v >= target)) break;
-            if ((++spins & 63) == 0 && *(volatile int*)err) { ok = 0; break; }
-            if (spins > kSpinLimit) {
-                if (lane == 0) atomicExch(err, 1);
-                ok = 0;
-                break;
-            }
-        }
-        if (lane == 0) s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// A whole shoot of `steps` RK4 steps in one cooperative launch: per stage, the
-// pair phase, a barrier, the RK4 stage of the particles this CTA owns
-// ([c n / G, (c+1) n / G)), and a barrier.
+// A whole shoot of `steps` RK4 steps in one cooperative launch (kernels other than
+// the 2-D Gaussian): per stage, the stream-K pair phase, a barrier, the RK4 stage
+// of the particles this CTA owns ([c n / G, (c+1) n / G)), and a barrier.
 template <int DIM, int KER, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
     k_shoot_mixed(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
@@ -582,13 +546,36 @@ __global__ void __launch_bounds__(THREADS, 1)
             a.stage = stage;
             a.S_in = stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
             a.S_out = stage == 1 ? Sb : Sa;
-            if constexpr (DIM == 2 && KER == EP_GAUSS) {
-                stage_pairs_gauss2<THREADS>(a, smem);
-            } else {
-                stage_pairs<DIM, KER, THREADS, false>(a, smem, nullptr);
-            }
+            stage_pairs<DIM, KER, THREADS, false>(a, smem, nullptr);
             if (!grid_barrier(bar, err, ++epoch)) return;
             for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<DIM>(a, i);
+            if (s == steps - 1 && stage == 3) break;
+            if (!grid_barrier(bar, err, ++epoch)) return;
+        }
+    }
+}
+
+// The stream-K 2-D Gaussian shoot: per stage, the pair phase over this CTA's range
+// of (tile of 128, source) units, a barrier, the RK4 stage of the particles the CTA
+// owns, and a barrier.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_shoot_streamk(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
+{
+    extern __shared__ float4 smem[];
+    const int n = a.n;
+    const int i0 = (int)((long long)blockIdx.x * n / gridDim.x), i1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
+    unsigned epoch = 0;
+    a.Sx = Sx;
+    for (int s = 0; s < steps; ++s) {
+        for (int stage = 0; stage < 4; ++stage) {
+            a.stage = stage;
+            a.S_in = stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
+            a.S_out = stage == 1 ? Sb : Sa;
+            stage_pairs_gauss2<THREADS>(a, smem);
+            if (!grid_barrier(bar, err, ++epoch)) return;
+            for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<2>(a, i);
+            if (s == steps - 1 && stage == 3) break;
             if (!grid_barrier(bar, err, ++epoch)) return;
         }
     }
@@ -873,28 +860,14 @@ bool allpairs_persistent_enabled()
     return v == 1;
 }
 
-StageArgs base_args(const ep_params& P, const AllPairsBufs& b, const APConfig& cfg)
-{
-    StageArgs a{};
-    const int ntiles = (b.n + kTileI - 1) / kTileI;
-    a.n = b.n;
-    a.U = (long long)ntiles * b.n;
-    a.G = (int)std::min<long long>(cfg.ctas, a.U);
-    const KernelScale ks = kernel_scale(P.kernel, P.sigma);
-    a.s = ks.s;
-    a.s_f = (float)ks.s;
-    a.dp_scale = ks.dp_scale;
-    a.dp_scale_f = (float)ks.dp_scale;
-    a.c0 = b.c0;
-    a.x = b.x;
-    a.acc = b.acc;
-    a.dacc = b.dacc;
-    a.K = b.K;
-    a.counters = b.counters;
-    return a;
-}
 
 }  // namespace
+
+static int tc_sm_count()
+{
+    DeviceInfo di{};
+    return device_info(&di) == EP_OK ? di.sm_count : 1;
+}
 
 size_t allpairs_bytes(int n, int dim, int prec)
 {
@@ -913,6 +886,7 @@ size_t allpairs_bytes(int n, int dim, int prec)
         const int V = dim == 2 ? 1 : 2;
         for (int k = 0; k < 3; ++k) z.add(sizeof(float4) * V * (size_t)n);
         z.add(sizeof(float) * 2 * dim * (size_t)n);
+        if (dim == 2) z.add(sizeof(float) * tc_part_floats(n, tc_sm_count()));
     } else {
         for (int k = 0; k < 3; ++k) z.add(sizeof(double) * 2 * dim * (size_t)n);
         z.add(sizeof(double) * 2 * dim * (size_t)n);
@@ -942,6 +916,7 @@ ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b)
         b->Sa = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
         b->Sb = (float4*)ar->carve(sizeof(float4) * V * (size_t)n);
         b->acc = (float*)ar->carve(sizeof(float) * 2 * dim * (size_t)n);
+        if (dim == 2) b->part = (float*)ar->carve(sizeof(float) * tc_part_floats(n, tc_sm_count()));
         if (!b->acc) return set_error("workspace too small"), EP_ENOMEM;
     } else {
         b->Dx = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
@@ -998,6 +973,10 @@ ep_status allpairs_load(const ep_params& P, const AllPairsBufs& b, const double*
 ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, double* dp, cudaStream_t st)
 {
     if (b.n == 0) return EP_OK;
+    // the tensor-core path needs the partial-sum buffer and reads its error flag back
+    // (a stream synchronisation); the fixed-scratch entry point carves neither
+    if (tc_enabled(P) && allpairs_persistent_enabled() && b.part && b.bar)
+        return tc_run(P, b, 0, 0.0, MODE_RHS, dq, dp, tc_sm_count(), st);
     const APConfig cfg = allpairs_config(b.n, P.dim, P.precision, P.kernel);
     StageArgs a = base_args(P, b, cfg);
     a.mode = MODE_RHS;
@@ -1011,6 +990,21 @@ ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, do
     return EP_OK;
 }
 
+// Launch of a whole persistent shoot; returns *done = false when the grid cannot
+// be co-resident (the caller then falls back to per-stage launches).
+ep_status finish_persistent(const AllPairsBufs& b, cudaStream_t st, bool* done)
+{
+    int herr = 0;
+    EP_TRY_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("persistent shoot: a grid-barrier wait gave up (kernel ended early)");
+        return EP_ETIMEOUT;
+    }
+    *done = true;
+    return EP_OK;
+}
+
 template <int DIM, int KER>
 ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
                              cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
@@ -1018,10 +1012,7 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
     constexpr int THREADS = 1024;
     constexpr int W = THREADS / 32;
     constexpr int V = DIM == 2 ? 1 : 2;
-    constexpr bool kFact = DIM == 2 && KER == EP_GAUSS;
-    const size_t smem = kFact ? std::max((size_t)kChunkG * (2 * sizeof(float4) + sizeof(float)),
-                                         (size_t)W * kKWidth * kTileG * sizeof(float))
-                              : std::max((size_t)kChunk * V * sizeof(float4), (size_t)W * kKWidth * kTileI * sizeof(float));
+    const size_t smem = std::max((size_t)kChunk * V * sizeof(float4), (size_t)W * kKWidth * kTileI * sizeof(float));
     auto fn = k_shoot_mixed<DIM, KER, THREADS>;
     static int resident = -1;
     if (resident < 0) {
@@ -1035,11 +1026,6 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
     *done = false;
     if (a0.G > resident) return EP_OK;  // not all CTAs can be resident: per-stage launches instead
     StageArgs a = a0;
-    if (kFact) {
-        // tiles of kTileG particles: units and CTA count of that decomposition
-        a.U = (long long)((b.n + kTileG - 1) / kTileG) * b.n;
-        a.G = (int)std::min<long long>(a.G, a.U);
-    }
     const float4* Sx = b.Sx;
     float4* Sa = b.Sa;
     float4* Sb = b.Sb;
@@ -1051,15 +1037,111 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
     if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
-    int herr = 0;
-    EP_TRY_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EP_TRY_CUDA(cudaStreamSynchronize(st));
-    if (herr) {
-        set_error("persistent shoot: a grid-barrier wait gave up (kernel ended early)");
-        return EP_ETIMEOUT;
+    return finish_persistent(b, st, done);
+}
+
+// The owner-computes 2-D Gaussian shoot: a.G CTAs, JL source lanes per row group.
+struct OwnerCfg {
+    int G = 0;
+    int JL = 4;
+};
+
+template <int JL>
+ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
+                       cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    constexpr int THREADS = 1024;
+    constexpr int W = THREADS / 32;
+    constexpr int R = (32 / JL) * 4;
+    const size_t smem = (size_t)kChunkG * (2 * sizeof(float4) + sizeof(float)) + (size_t)(W + 1) * kKWidth * R * sizeof(float);
+    auto fn = k_shoot_owner<THREADS, JL>;
+    static int resident = -1;
+    if (resident < 0) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, smem));
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        resident = per_sm * di.sm_count;
     }
-    *done = true;
-    return EP_OK;
+    *done = false;
+    StageArgs a = a0;
+    a.G = std::max(1, std::min(a.G, a.n));
+    if (a.G > resident) return EP_OK;
+    const float4* Sx = b.Sx;
+    float4* Sa = b.Sa;
+    float4* Sb = b.Sb;
+    unsigned* bar = b.bar;
+    int* err = b.err;
+    EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
+    count_launch();
+    if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
+    EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
+    if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
+    return finish_persistent(b, st, done);
+}
+
+// The stream-K 2-D Gaussian shoot over a.G CTAs (tiles of kTileG).
+ep_status launch_streamk(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
+                         cudaEvent_t ev0, cudaEvent_t ev1)
+{
+    constexpr int THREADS = 1024;
+    constexpr int W = THREADS / 32;
+    const size_t smem = std::max((size_t)kChunkG * (2 * sizeof(float4) + sizeof(float)),
+                                 (size_t)W * kKWidth * kTileG * sizeof(float));
+    auto fn = k_shoot_streamk<THREADS>;
+    static int resident = -1;
+    if (resident < 0) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, smem));
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        resident = per_sm * di.sm_count;
+    }
+    *done = false;
+    StageArgs a = a0;
+    a.U = (long long)((b.n + kTileG - 1) / kTileG) * b.n;
+    a.G = (int)std::max<long long>(1, std::min<long long>(a.G, a.U));
+    if (a.G > resident) return EP_OK;
+    const float4* Sx = b.Sx;
+    float4* Sa = b.Sa;
+    float4* Sb = b.Sb;
+    unsigned* bar = b.bar;
+    int* err = b.err;
+    EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
+    count_launch();
+    if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
+    EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
+    if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
+    return finish_persistent(b, st, done);
+}
+
+// JL = 1, 4, 16: owner computes with that many source lanes; JL = 0: stream-K.
+ep_status launch_owner_cfg(const StageArgs& a, const AllPairsBufs& b, int steps, const OwnerCfg& c, cudaStream_t st,
+                           bool* done, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
+{
+    StageArgs a2 = a;
+    a2.G = c.G;
+    if (c.JL == 0) return launch_streamk(a2, b, steps, st, done, ev0, ev1);
+    if (c.JL == 1) return launch_owner<1>(a2, b, steps, st, done, ev0, ev1);
+    if (c.JL == 16) return launch_owner<16>(a2, b, steps, st, done, ev0, ev1);
+    return launch_owner<4>(a2, b, steps, st, done, ev0, ev1);
+}
+
+// Default owner configuration: the widest sub-tile the rows per SM fill, and the
+// CTA count that fills each CTA's sub-tiles.
+OwnerCfg owner_default(int n, int sm)
+{
+    OwnerCfg c;
+    const double per = (double)n / sm;
+    c.JL = per >= 96 ? 1 : per >= 24 ? 4 : 16;
+    const int R = (32 / c.JL) * 4;
+    const long long k = std::max<long long>(1, (n + (long long)sm * R - 1) / ((long long)sm * R));
+    c.G = (int)std::max<long long>(1, std::min<long long>(sm, (n + k * R - 1) / (k * R)));
+    return c;
 }
 
 ep_status launch_shoot(const ep_params& P, const StageArgs& a, const AllPairsBufs& b, int steps, cudaStream_t st,
@@ -1067,7 +1149,7 @@ ep_status launch_shoot(const ep_params& P, const StageArgs& a, const AllPairsBuf
 {
 #define EP_SHOOT_CASE(D, K) \
     if (P.dim == D && P.kernel == K) return launch_shoot_mixed<D, K>(a, b, steps, st, done, ev0, ev1);
-    EP_SHOOT_CASE(2, EP_GAUSS) EP_SHOOT_CASE(2, EP_TENT) EP_SHOOT_CASE(2, EP_EXPCONE)
+    EP_SHOOT_CASE(2, EP_TENT) EP_SHOOT_CASE(2, EP_EXPCONE)
     EP_SHOOT_CASE(3, EP_GAUSS) EP_SHOOT_CASE(3, EP_TENT) EP_SHOOT_CASE(3, EP_EXPCONE)
 #undef EP_SHOOT_CASE
     *done = false;
@@ -1075,22 +1157,29 @@ ep_status launch_shoot(const ep_params& P, const StageArgs& a, const AllPairsBuf
 }
 
 // ------------------------------------------------------------------ autotuner
-// The persistent 2-D Gaussian shoot splits the pair matrix (tiles of kTileG x n)
-// over G CTAs.  G = SM count balances the work exactly but lets some CTAs span two
-// tiles (each segment start costs a round of loads and a reduction); a G that is a
-// multiple of the tile count keeps every CTA inside one tile at the price of idle
-// SMs.  The tuner times a one-step shoot for each candidate on the loaded state
-// (restoring it afterwards) and caches the fastest per (n, dim, kernel).
-// EP_AUTOTUNE=0 in the environment skips it (G = SM count).
+// The persistent 2-D Gaussian shoot has two designs and free parameters: owner
+// computes with a CTA count G (rows per CTA = n / G) and a sub-tile width (JL
+// source lanes: 128, 32 or 8 rows per sub-tile), where a sub-tile costs a staging
+// pass over all n sources and a reduction, a partly filled sub-tile wastes lanes
+// and fewer CTAs leave SMs idle; and stream-K over G CTAs (JL = 0), which splits
+// the pair matrix evenly at the price of FP64 atomics and a second barrier.
+// The tuner times a one-step shoot for each candidate on the loaded state
+// (restoring it afterwards) and caches the fastest per (n, device).  The tensor-core
+// path (opt-in) is tuned over its CTA count the same way.  EP_AUTOTUNE=0 in the
+// environment skips tuning (owner_default).
 struct TuneKey {
-    int n, dim, kernel, dev;
+    int n, dim, kernel, dev, tc;
     bool operator<(const TuneKey& o) const
     {
-        return n != o.n ? n < o.n : dim != o.dim ? dim < o.dim : kernel != o.kernel ? kernel < o.kernel : dev < o.dev;
+        if (n != o.n) return n < o.n;
+        if (dim != o.dim) return dim < o.dim;
+        if (kernel != o.kernel) return kernel < o.kernel;
+        if (dev != o.dev) return dev < o.dev;
+        return tc < o.tc;
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tuned;
+std::map<TuneKey, OwnerCfg> g_tuned;
 
 bool autotune_enabled()
 {
@@ -1098,18 +1187,32 @@ bool autotune_enabled()
     return !(e && e[0] == '0');
 }
 
-ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a, double dt, cudaStream_t st, int* best)
+ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a, double dt, cudaStream_t st,
+                          OwnerCfg* best, bool tc)
 {
     DeviceInfo di{};
     EP_TRY(device_info(&di));
     const int sm = di.sm_count;
-    const int ntiles = (b.n + kTileG - 1) / kTileG;
-    // the default split, the full and 7/8 SM counts, the two largest tile-aligned counts
-    std::vector<int> cand = {a.G, sm, sm - sm / 8};
-    for (int k = sm / std::max(1, ntiles), c = 0; k >= 1 && c < 2; --k, ++c) cand.push_back(ntiles * k);
-    for (int& g : cand) g = (int)std::min<long long>(g, a.U);
-    std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    const int n = b.n;
+    std::vector<OwnerCfg> cand;
+    if (tc) {
+        const int tiles = tc_tiles(n);
+        std::vector<int> gs = {sm, sm - sm / 8};
+        for (int k = sm / std::max(1, tiles), c = 0; k >= 1 && c < 2; --k, ++c) gs.push_back(tiles * k);
+        for (int g : gs) cand.push_back(OwnerCfg{g, 0});
+    } else {
+        for (int JL : {1, 4, 16}) {
+            const int R = (32 / JL) * 4;
+            const long long k = std::max<long long>(1, (n + (long long)sm * R - 1) / ((long long)sm * R));
+            const int g1 = (int)std::max<long long>(1, std::min<long long>(sm, (n + k * R - 1) / (k * R)));
+            cand.push_back(OwnerCfg{g1, JL});
+            if (g1 != std::min(sm, n)) cand.push_back(OwnerCfg{std::min(sm, n), JL});
+        }
+        // stream-K: the full SM count and the largest tile-aligned count
+        const int tiles = (n + kTileG - 1) / kTileG;
+        cand.push_back(OwnerCfg{sm, 0});
+        if (tiles <= sm) cand.push_back(OwnerCfg{tiles * (sm / tiles), 0});
+    }
     const size_t m2 = 2 * (size_t)P.dim * b.n;
     EP_TRY_CUDA(cudaMemcpyAsync(b.x_bak, b.x, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
     EP_TRY_CUDA(cudaMemcpyAsync(b.S_bak, b.Sx, sizeof(float4) * (size_t)b.n, cudaMemcpyDeviceToDevice, st));
@@ -1117,33 +1220,41 @@ ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a
     EP_TRY_CUDA(cudaEventCreate(&e0));
     EP_TRY_CUDA(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    *best = sm;
+    *best = tc ? OwnerCfg{sm, 0} : owner_default(n, sm);
     a.dt = dt;
     a.dt_f = (float)dt;
-    for (int G : cand) {
-        if (G < 1) continue;
-        a.G = G;
+    ep_status out = EP_OK;
+    for (const OwnerCfg& c : cand) {
+        if (c.G < 1) continue;
         float ms = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             EP_TRY_CUDA(cudaMemcpyAsync(b.x, b.x_bak, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
             EP_TRY_CUDA(cudaMemcpyAsync(b.Sx, b.S_bak, sizeof(float4) * (size_t)b.n, cudaMemcpyDeviceToDevice, st));
             bool done = false;
-            ep_status s = launch_shoot(P, a, b, 1, st, &done, e0, e1);
+            ep_status s = EP_OK;
+            if (tc) {
+                s = tc_run(P, b, 1, dt, MODE_RK4, nullptr, nullptr, c.G, st, e0, e1);
+                done = s == EP_OK;
+            } else {
+                s = launch_owner_cfg(a, b, 1, c, st, &done, e0, e1);
+            }
+            if (s == EP_ETIMEOUT) out = s;
             if (s != EP_OK || !done) break;
             float t = 0.f;
             EP_TRY_CUDA(cudaEventElapsedTime(&t, e0, e1));
             if (rep > 0) ms = std::min(ms, t);
         }
+        if (out != EP_OK) break;
         if (ms < best_ms) {
             best_ms = ms;
-            *best = G;
+            *best = c;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     EP_TRY_CUDA(cudaMemcpyAsync(b.x, b.x_bak, sizeof(double) * m2, cudaMemcpyDeviceToDevice, st));
     EP_TRY_CUDA(cudaMemcpyAsync(b.Sx, b.S_bak, sizeof(float4) * (size_t)b.n, cudaMemcpyDeviceToDevice, st));
-    return EP_OK;
+    return out;
 }
 
 ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt, cudaStream_t st)
@@ -1156,26 +1267,34 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
     a.dt_f = (float)dt;
     if (P.precision == EP_MIXED && cfg.threads == 1024 && allpairs_persistent_enabled()) {
         a.Sx_w = b.Sx;
-        if (P.dim == 2 && P.kernel == EP_GAUSS && b.x_bak && autotune_enabled()) {
+        if (P.dim == 2 && P.kernel == EP_GAUSS) {
+            const bool tc = tc_enabled(P) && b.part;
             DeviceInfo di{};
             EP_TRY(device_info(&di));
-            const TuneKey key{b.n, P.dim, P.kernel, di.device};
-            int G = -1;
-            {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                auto it = g_tuned.find(key);
-                if (it != g_tuned.end()) G = it->second;
+            OwnerCfg c = tc ? OwnerCfg{di.sm_count, 0} : owner_default(b.n, di.sm_count);
+            if (b.x_bak && autotune_enabled()) {
+                const TuneKey key{b.n, P.dim, P.kernel, di.device, tc ? 1 : 0};
+                bool have = false;
+                {
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    auto it = g_tuned.find(key);
+                    if (it != g_tuned.end()) c = it->second, have = true;
+                }
+                if (!have) {
+                    EP_TRY(tune_persistent(P, b, a, dt, st, &c, tc));
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tuned[key] = c;
+                }
             }
-            if (G < 0) {
-                EP_TRY(tune_persistent(P, b, a, dt, st, &G));
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tuned[key] = G;
-            }
-            a.G = G;
+            if (tc) return tc_run(P, b, steps, dt, MODE_RK4, nullptr, nullptr, c.G, st);
+            bool done = false;
+            EP_TRY(launch_owner_cfg(a, b, steps, c, st, &done));
+            if (done) return EP_OK;
+        } else {
+            bool done = false;
+            EP_TRY(launch_shoot(P, a, b, steps, st, &done));
+            if (done) return EP_OK;
         }
-        bool done = false;
-        EP_TRY(launch_shoot(P, a, b, steps, st, &done));
-        if (done) return EP_OK;
     }
     a.Sx = b.Sx;
     a.Sx_w = b.Sx;

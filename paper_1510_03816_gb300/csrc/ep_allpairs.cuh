@@ -24,6 +24,7 @@ struct AllPairsBufs {
     float4* Sa = nullptr;    // stage copies (ping-pong)
     float4* Sb = nullptr;
     float* acc = nullptr;    // FP32 RK4 accumulator, n * 2 * dim
+    float* part = nullptr;   // per-(CTA, tile) partial sums of the tensor-core path (2-D mixed)
     // fp64
     double* Dx = nullptr;
     double* Da = nullptr;
@@ -57,5 +58,16 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
 // copy 4*steps the final state.  rec / drec hold 4*steps + 1 stage copies.
 ep_status allpairs_steps_rec(const ep_params& P, const AllPairsBufs& b, int steps, double dt, float4* rec,
                              double* drec, cudaStream_t st);
+
+// Tensor-core (tcgen05) persistent path of the 2-D Gaussian in mixed precision
+// (ep_tc.cu).  Opt-in: EP_TC=1 in the environment selects it (the CUDA-core path
+// is faster for this contraction, see ep_tc.cu).
+bool tc_enabled(const ep_params& P);
+int tc_tiles(int n);
+size_t tc_part_floats(int n, int sm_count);
+// mode MODE_RK4: `steps` RK4 steps of size dt from the state in x (x, Sx updated);
+// mode MODE_RHS: one RHS at Sx into out_q, out_p.  G = requested CTA count.
+ep_status tc_run(const ep_params& P, const AllPairsBufs& b, int steps, double dt, int mode, double* out_q,
+                 double* out_p, int G, cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 
 }  // namespace ep
