@@ -216,20 +216,21 @@ def run_gb300(args):
     value = total_pairs / (t_max / 1e3)
 
     # ---- dominant kernel: the persistent shoot (one cooperative launch per shoot,
-    # 4 x 100 RK4 stages inside), timed on the launch stream
+    # 4 x 100 RK4 stages inside), its launches timed by the library with CUDA events
+    # recorded on the launch stream around the cooperative launch
     p_fin = last.p0
-    R = 3
-    for _ in range(1):
-        ep.shoot(X, p_fin, prm)
+    R = 5
+    ep.shoot(X, p_fin, prm)
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
+    ep.set_launch_timing(True)
+    launch_times, kernel_name = [], ""
     for _ in range(R):
         q1m, _p1m = ep.shoot(X, p_fin, prm)
-    b.record(stream)
-    torch.cuda.synchronize()
-    shoot_ms = a.elapsed_time(b) / R
-    launch_ms = shoot_ms
+        t_ms, kernel_name = ep.last_launch()
+        launch_times.append(t_ms)
+    ep.set_launch_timing(False)
+    launch_ms = float(np.mean(launch_times))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
     achieved = FLOPS_PER_PAIR_2D_GAUSS * n * n * 4 * S / (launch_ms / 1e3) / 1e12
@@ -267,7 +268,7 @@ def run_gb300(args):
         "shoots_per_s": world * shoots / (t_max / 1e3),
         "endpoint_err_vs_fp64": err,
         "fp64_shoots_per_s": 1e3 / fp64_ms,
-        "roofline": {"bound": "alu", "kernel": "k_shoot_mixed<2,GAUSS,1024> (persistent all-pairs shoot, 400 fused RK4 stages per launch)",
+        "roofline": {"bound": "alu", "kernel": f"{kernel_name}: persistent all-pairs shoot, {4 * S} fused RK4 stages per launch",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": None, "launch_us": launch_ms * 1e3, "stage_us": launch_ms * 1e3 / (4 * S),
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)",

@@ -179,6 +179,16 @@ int64_t ep_launch_count(void);
 /* Library version: major * 10000 + minor * 100 + patch. */
 int ep_version(void);
 
+/* Launch timing of the persistent all-pairs shoot (the fused RK4 integration of
+ * Sec. 4; one cooperative launch per ep_shoot and per feedback iterate of
+ * ep_match).  With timing on, CUDA events are recorded on the caller's stream
+ * around that launch: ep_last_launch_ms() returns the duration of the last timed
+ * launch in milliseconds (-1 if none) and ep_last_launch_kernel() the name of its
+ * kernel ("" if none).  Off by default; the setting is process-wide. */
+void ep_set_launch_timing(int on);
+double ep_last_launch_ms(void);
+const char* ep_last_launch_kernel(void);
+
 #ifdef __cplusplus
 }
 #endif

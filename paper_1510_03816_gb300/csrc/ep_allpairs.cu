@@ -22,6 +22,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -187,18 +188,42 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 constexpr int kChunkG = 2048;
 constexpr float kFactorMax = 60.0f;
 
+// Inputs of the RK4 stage of one component of one owned particle: the stage input
+// momentum (for the dp contraction), the step-start stage copy, the RK4
+// accumulator and (stage 3) the FP64 state.
+struct EpiIn {
+    float2 pin;
+    float xs;
+    float A;
+    double xv;
+};
+
+__device__ __forceinline__ double* epi_state(const StageArgs& a, int i, int comp)
+{
+    return comp < 2 ? a.x + (size_t)i * 2 + comp : a.x + (size_t)a.n * 2 + (size_t)i * 2 + (comp - 2);
+}
+
+__device__ __forceinline__ EpiIn epi_load(const StageArgs& a, int i, int comp)
+{
+    EpiIn e;
+    e.pin = __ldcg(reinterpret_cast<const float2*>(a.S_in + i) + 1);
+    e.xs = __ldcg(reinterpret_cast<const float*>(a.Sx + i) + comp);
+    e.A = a.acc[(size_t)i * 4 + comp];
+    e.xv = a.stage == 3 ? *epi_state(a, i, comp) : 0.0;
+    return e;
+}
+
 // RK4 stage of component comp (0, 1: q; 2, 3: p) of particle i from its six FP32
 // pair sums f (dq_x, dq_y, M_xx, M_xy, M_yx, M_yy): the 2-D mixed epilogue with
 // one thread per component.  Only the step update (stage 3) touches FP64.
-__device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int comp, const float* f)
+__device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int comp, const float* f, const EpiIn& e)
 {
     float kv;
     if (comp < 2) {
         kv = comp == 0 ? f[0] : f[1];
     } else {
-        const float2 pin = __ldcg(reinterpret_cast<const float2*>(a.S_in + i) + 1);
         const float m0 = comp == 2 ? f[2] : f[4], m1 = comp == 2 ? f[3] : f[5];
-        kv = a.dp_scale_f * fmaf(m0, pin.x, m1 * pin.y);
+        kv = a.dp_scale_f * fmaf(m0, e.pin.x, m1 * e.pin.y);
     }
     if (a.mode == MODE_RHS) {
         double* out = comp < 2 ? a.out_q : a.out_p;
@@ -208,17 +233,29 @@ __device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int co
     float* A = a.acc + (size_t)i * 4 + comp;
     if (a.stage < 3) {
         const float cdt = (a.stage == 2 ? 1.0f : 0.5f) * a.dt_f;
-        const float xs = reinterpret_cast<const float*>(a.Sx + i)[comp];
-        const float y = fmaf(comp < 2 ? cdt * a.s_f : cdt, kv, xs);
-        *A = a.stage == 0 ? kv : fmaf(2.0f, kv, *A);  // k1 + 2 k2 + 2 k3
+        const float y = fmaf(comp < 2 ? cdt * a.s_f : cdt, kv, e.xs);
+        *A = a.stage == 0 ? kv : fmaf(2.0f, kv, e.A);  // k1 + 2 k2 + 2 k3
         reinterpret_cast<float*>(a.S_out + i)[comp] = y;
     } else {
-        const int n = a.n;
-        double* xv = comp < 2 ? a.x + (size_t)i * 2 + comp : a.x + (size_t)n * 2 + (size_t)i * 2 + (comp - 2);
-        const double nv = *xv + (double)(a.dt_f * (1.0f / 6.0f) * (*A + kv));
-        *xv = nv;
+        const double nv = e.xv + (double)(a.dt_f * (1.0f / 6.0f) * (e.A + kv));
+        *epi_state(a, i, comp) = nv;
         reinterpret_cast<float*>(a.Sx_w + i)[comp] = comp < 2 ? (float)((nv - a.c0[comp]) * a.s) : (float)nv;
     }
+}
+
+// Sources staged per shared-memory fill of the owner kernel: all of them up to
+// 4096 when the sub-tile is narrow (JL >= 4), 2048 with 128-row sub-tiles (whose
+// reduction buffer is larger).
+template <int JL>
+__host__ __device__ constexpr int owner_chunk()
+{
+    return JL == 1 ? 2048 : 4096;
+}
+template <int THREADS, int JL>
+constexpr size_t owner_smem()
+{
+    return (size_t)owner_chunk<JL>() * (2 * sizeof(float4) + sizeof(float)) +
+           (size_t)(THREADS / 32 + 1) * kKWidth * ((32 / JL) * 4) * sizeof(float);
 }
 
 template <int THREADS, int JL>
@@ -228,16 +265,19 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
     constexpr int RI = 4;
     constexpr int RG = 32 / JL;  // row groups per warp
     constexpr int R = RG * RI;   // rows per sub-tile
-    float4* recA = smem;                                         // [2 * kChunkG]
-    float* recB = reinterpret_cast<float*>(smem + 2 * kChunkG);  // [kChunkG]
-    float* red = reinterpret_cast<float*>(smem + 2 * kChunkG) + kChunkG;  // [W][6][R], then [6][R]
+    constexpr int CH = owner_chunk<JL>();
+    constexpr int NV = RI * kKWidth;  // finalized partials per lane
+    float4* recA = smem;                                    // [2 * CH]
+    float* recB = reinterpret_cast<float*>(smem + 2 * CH);  // [CH]
+    float* red = recB + CH;                                 // [W][6][R], then fin [6][R]
+    float* fin = red + (size_t)W * kKWidth * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rg = lane / JL, jl = lane % JL;
     const int n = a.n;
     for (int t0 = r0; t0 < r1; t0 += R) {
         const int t1 = min(r1, t0 + R);
-        constexpr int PF = kChunkG / THREADS;
-        const int L0 = min(kChunkG, n);
+        constexpr int PF = CH / THREADS < 2 ? CH / THREADS : 2;  // sources prefetched per thread
+        const int L0 = min(PF * THREADS, n);
         float4 pre[PF];
 #pragma unroll
         for (int k = 0; k < PF; ++k) {
@@ -259,11 +299,11 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
         float2 sqv[RI], sbx[RI], sby[RI];
 #pragma unroll
         for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
-        for (int cj = 0; cj < n; cj += kChunkG) {
-            const int L = min(kChunkG, n - cj);
-            __syncthreads();
+        for (int cj = 0; cj < n; cj += CH) {
+            const int L = min(CH, n - cj);
+            if (cj > 0) __syncthreads();
             for (int t = threadIdx.x; t < L; t += THREADS) {
-                const float4 v = cj == 0 ? pre[t / THREADS] : __ldcg(a.S_in + cj + t);
+                const float4 v = cj == 0 && t < PF * THREADS ? pre[t / THREADS] : __ldcg(a.S_in + cj + t);
                 const float x = v.x - c4.x, y = v.y - c4.y;
                 recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), y * v.z);
                 recA[2 * t + 1] = make_float4(v.z, v.w, x * v.z, x * v.w);
@@ -306,42 +346,71 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
                 }
             }
         }
-        // source lanes -> lane jl == 0 of each row group
+        // finalize the lane's partials (linear in the sums, so before the reduction):
+        // per row dq = E sq, M = q'' (x) dq - E sb (E = 1 in the difference form)
+        float v[NV];
 #pragma unroll
-        for (int off = 1; off < JL; off <<= 1) {
+        for (int r = 0; r < RI; ++r) {
+            const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
+            const float d0 = E * sqv[r].x, d1 = E * sqv[r].y;
+            v[r * kKWidth + 0] = d0;
+            v[r * kKWidth + 1] = d1;
+            v[r * kKWidth + 2] = fmaf(qx[r], d0, -E * sbx[r].x);
+            v[r * kKWidth + 3] = fmaf(qx[r], d1, -E * sbx[r].y);
+            v[r * kKWidth + 4] = fmaf(qy[r], d0, -E * sby[r].x);
+            v[r * kKWidth + 5] = fmaf(qy[r], d1, -E * sby[r].y);
+        }
+        // reduce-scatter over the JL source lanes: each round halves the values a lane
+        // holds (it keeps one half, adds the partner's copy of it); the last round of an
+        // odd count adds the partner's values whole.  Afterwards lane jl holds, of the
+        // 4 x 6 values, the block selected by its bits (high bit first).
+        int first = 0;  // index (into the original 24) of the lane's first value
+        int cnt = NV;
 #pragma unroll
-            for (int r = 0; r < RI; ++r) {
-                sqv[r].x += __shfl_xor_sync(0xffffffffu, sqv[r].x, off);
-                sqv[r].y += __shfl_xor_sync(0xffffffffu, sqv[r].y, off);
-                sbx[r].x += __shfl_xor_sync(0xffffffffu, sbx[r].x, off);
-                sbx[r].y += __shfl_xor_sync(0xffffffffu, sbx[r].y, off);
-                sby[r].x += __shfl_xor_sync(0xffffffffu, sby[r].x, off);
-                sby[r].y += __shfl_xor_sync(0xffffffffu, sby[r].y, off);
+        for (int o = JL / 2; o >= 1; o >>= 1) {
+            if (cnt % 2 == 0) {
+                const int h = cnt / 2;
+                const bool upper = (jl & o) != 0;
+#pragma unroll
+                for (int k = 0; k < NV / 2; ++k) {
+                    if (k < h) {
+                        const float send = upper ? v[k] : v[k + h];
+                        const float keep = upper ? v[k + h] : v[k];
+                        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    }
+                }
+                if (upper) first += h;
+                cnt = h;
+            } else {
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    if (k < cnt) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
             }
         }
-        // per row: dq = E sq, M = q'' (x) dq - E sb (E = 1 in the difference form);
-        // the warps' partials go to shared memory [W][6][R]
-        if (jl == 0) {
+        // the lane's values -> red[warp][k][row]; the value at original index e is row
+        // e / 6 (lane row rg + RG * (e / 6)), component e % 6
+        const bool writer = (NV % JL == 0) || (jl & 1) == 0;  // odd final count: pairs hold copies
+        if (writer) {
 #pragma unroll
-            for (int r = 0; r < RI; ++r) {
-                const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
-                const float d0 = E * sqv[r].x, d1 = E * sqv[r].y;
-                float* o = red + (size_t)warp * kKWidth * R + rg + RG * r;
-                o[0 * R] = d0;
-                o[1 * R] = d1;
-                o[2 * R] = fmaf(qx[r], d0, -E * sbx[r].x);
-                o[3 * R] = fmaf(qx[r], d1, -E * sbx[r].y);
-                o[4 * R] = fmaf(qy[r], d0, -E * sby[r].x);
-                o[5 * R] = fmaf(qy[r], d1, -E * sby[r].y);
+            for (int k = 0; k < NV; ++k) {
+                if (k < cnt) {
+                    const int e = first + k;
+                    red[(size_t)warp * kKWidth * R + (e % kKWidth) * R + rg + RG * (e / kKWidth)] = v[k];
+                }
             }
         }
         __syncthreads();
-        float* fin = red + (size_t)W * kKWidth * R;  // [6][R]
-        for (int t = threadIdx.x; t < kKWidth * R; t += THREADS) {
+        // sum over the warps: QS threads per output value
+        constexpr int NOUT = kKWidth * R;
+        constexpr int QS = (THREADS / NOUT) >= 8 ? 8 : (THREADS / NOUT) >= 4 ? 4 : (THREADS / NOUT) >= 2 ? 2 : 1;
+        for (int t = threadIdx.x; t < NOUT * QS; t += THREADS) {
+            const int o = t / QS, q = t % QS;
             float sum = 0.0f;
-#pragma unroll 8
-            for (int w2 = 0; w2 < W; ++w2) sum += red[w2 * kKWidth * R + t];
-            fin[t] = sum;
+#pragma unroll
+            for (int w2 = q; w2 < W; w2 += QS) sum += red[w2 * NOUT + o];
+#pragma unroll
+            for (int m = QS / 2; m >= 1; m >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, m);
+            if (q == 0) fin[o] = sum;
         }
         __syncthreads();
         // the RK4 stage of the sub-tile's rows, one thread per component
@@ -352,9 +421,10 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
                 float f[kKWidth];
 #pragma unroll
                 for (int k = 0; k < kKWidth; ++k) f[k] = fin[k * R + rl];
-                epilogue2_comp(a, i, comp, f);
+                epilogue2_comp(a, i, comp, f, epi_load(a, i, comp));
             }
         }
+        if (t0 + R < r1) __syncthreads();  // the next sub-tile restages the shared buffers
     }
 }
 
@@ -863,6 +933,28 @@ bool allpairs_persistent_enabled()
 
 }  // namespace
 
+static std::atomic<int> g_timing{0};
+static std::mutex g_timing_mu;
+static double g_last_ms = -1.0;
+static char g_last_kernel[64] = "";
+
+bool launch_timing_enabled() { return g_timing.load(std::memory_order_relaxed) != 0; }
+void set_launch_timing(bool on) { g_timing.store(on ? 1 : 0, std::memory_order_relaxed); }
+void record_launch_time(cudaEvent_t e0, cudaEvent_t e1, const char* kernel)
+{
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ms = -1.0f;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_last_ms = ms;
+    snprintf(g_last_kernel, sizeof(g_last_kernel), "%s", kernel);
+}
+double last_launch_ms()
+{
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    return g_last_ms;
+}
+const char* last_launch_kernel() { return g_last_kernel; }
+
 static int tc_sm_count()
 {
     DeviceInfo di{};
@@ -1051,9 +1143,7 @@ ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cu
                        cudaEvent_t ev0, cudaEvent_t ev1)
 {
     constexpr int THREADS = 1024;
-    constexpr int W = THREADS / 32;
-    constexpr int R = (32 / JL) * 4;
-    const size_t smem = (size_t)kChunkG * (2 * sizeof(float4) + sizeof(float)) + (size_t)(W + 1) * kKWidth * R * sizeof(float);
+    const size_t smem = owner_smem<THREADS, JL>();
     auto fn = k_shoot_owner<THREADS, JL>;
     static int resident = -1;
     if (resident < 0) {
@@ -1257,6 +1347,27 @@ ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a
     return out;
 }
 
+// CUDA events around one persistent launch when launch timing is on (null otherwise).
+struct TimedLaunch {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TimedLaunch()
+    {
+        if (launch_timing_enabled() && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+            if (e0) cudaEventDestroy(e0);
+            e0 = e1 = nullptr;
+        }
+    }
+    void record(const char* kernel) const
+    {
+        if (e0) record_launch_time(e0, e1, kernel);  // the launch functions synchronised the stream
+    }
+    ~TimedLaunch()
+    {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt, cudaStream_t st)
 {
     if (b.n == 0 || steps == 0) return EP_OK;
@@ -1286,14 +1397,34 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
                     g_tuned[key] = c;
                 }
             }
-            if (tc) return tc_run(P, b, steps, dt, MODE_RK4, nullptr, nullptr, c.G, st);
+            TimedLaunch tl;
             bool done = false;
-            EP_TRY(launch_owner_cfg(a, b, steps, c, st, &done));
-            if (done) return EP_OK;
+            char name[64];
+            if (tc) {
+                EP_TRY(tc_run(P, b, steps, dt, MODE_RK4, nullptr, nullptr, c.G, st, tl.e0, tl.e1));
+                done = true;
+                snprintf(name, sizeof(name), "k_shoot_tc (G=%d)", c.G);
+            } else {
+                EP_TRY(launch_owner_cfg(a, b, steps, c, st, &done, tl.e0, tl.e1));
+                if (c.JL == 0)
+                    snprintf(name, sizeof(name), "k_shoot_streamk<1024> (G=%d)", c.G);
+                else
+                    snprintf(name, sizeof(name), "k_shoot_owner<1024,%d> (G=%d)", c.JL, std::min(c.G, b.n));
+            }
+            if (done) {
+                tl.record(name);
+                return EP_OK;
+            }
         } else {
+            TimedLaunch tl;
             bool done = false;
-            EP_TRY(launch_shoot(P, a, b, steps, st, &done));
-            if (done) return EP_OK;
+            EP_TRY(launch_shoot(P, a, b, steps, st, &done, tl.e0, tl.e1));
+            if (done) {
+                char name[64];
+                snprintf(name, sizeof(name), "k_shoot_mixed<%d,%d,1024> (G=%d)", P.dim, P.kernel, a.G);
+                tl.record(name);
+                return EP_OK;
+            }
         }
     }
     a.Sx = b.Sx;

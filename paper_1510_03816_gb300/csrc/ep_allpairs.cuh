@@ -59,6 +59,14 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
 ep_status allpairs_steps_rec(const ep_params& P, const AllPairsBufs& b, int steps, double dt, float4* rec,
                              double* drec, cudaStream_t st);
 
+// Launch timing of the persistent shoot (ep_set_launch_timing): when on, the
+// launch functions record CUDA events around the cooperative launch.
+bool launch_timing_enabled();
+void set_launch_timing(bool on);
+void record_launch_time(cudaEvent_t e0, cudaEvent_t e1, const char* kernel);
+double last_launch_ms();
+const char* last_launch_kernel();
+
 // Tensor-core (tcgen05) persistent path of the 2-D Gaussian in mixed precision
 // (ep_tc.cu).  Opt-in: EP_TC=1 in the environment selects it (the CUDA-core path
 // is faster for this contraction, see ep_tc.cu).

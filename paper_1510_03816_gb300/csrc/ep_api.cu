@@ -345,6 +345,12 @@ int ep_version(void) { return 10000; }
 
 int64_t ep_launch_count(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+void ep_set_launch_timing(int on) { set_launch_timing(on != 0); }
+
+double ep_last_launch_ms(void) { return last_launch_ms(); }
+
+const char* ep_last_launch_kernel(void) { return last_launch_kernel(); }
+
 const char* ep_last_error(void) { return g_err; }
 
 ep_status ep_release_workspace(void) { return release_all_arenas(); }

@@ -33,7 +33,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libep.so")
 # Every symbol include/ep.h declares (checked by the ABI test).
 EXPORTS = ("ep_rhs", "ep_shoot", "ep_match", "ep_adjoint", "ep_match_batched", "ep_hamiltonian",
            "ep_hvp", "ep_cell_neighbors", "ep_release_workspace", "ep_last_error", "ep_version",
-           "ep_launch_count", "ep_rhs_noalloc")
+           "ep_launch_count", "ep_rhs_noalloc", "ep_set_launch_timing", "ep_last_launch_ms",
+           "ep_last_launch_kernel")
 
 
 class EPError(RuntimeError):
@@ -101,6 +102,12 @@ def load():
     lib.ep_version.argtypes = []
     lib.ep_launch_count.restype = ctypes.c_int64
     lib.ep_launch_count.argtypes = []
+    lib.ep_set_launch_timing.restype = None
+    lib.ep_set_launch_timing.argtypes = [ctypes.c_int]
+    lib.ep_last_launch_ms.restype = ctypes.c_double
+    lib.ep_last_launch_ms.argtypes = []
+    lib.ep_last_launch_kernel.restype = ctypes.c_char_p
+    lib.ep_last_launch_kernel.argtypes = []
     _lib = lib
     return lib
 
@@ -116,6 +123,17 @@ def version() -> int:
 def launch_count() -> int:
     """Kernels libep.so has launched in this process (ep_launch_count)."""
     return int(load().ep_launch_count())
+
+
+def set_launch_timing(on: bool) -> None:
+    """Record CUDA events around each persistent shoot launch (ep_set_launch_timing)."""
+    load().ep_set_launch_timing(1 if on else 0)
+
+
+def last_launch() -> tuple[float, str]:
+    """(duration in ms, kernel name) of the last timed persistent shoot launch."""
+    lib = load()
+    return float(lib.ep_last_launch_ms()), lib.ep_last_launch_kernel().decode()
 
 
 def release_workspace() -> None:

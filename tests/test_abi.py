@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "ep.h")
 
 def declared_symbols():
     src = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:ep_status|const char\s*\*|int64_t|int)\s+(ep_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:ep_status|const char\s*\*|int64_t|int|void|double)\s+(ep_\w+)\s*\(", src, re.M)))
 
 
 @pytest.fixture(scope="module")
