@@ -47,6 +47,9 @@ METRIC = "pair interactions/s in EP RHS; shoots/s to 1e-6 endpoint err vs plain 
 UNIT = "pair interactions/s"
 FP32_LANES_PER_SM = 128
 FLOPS_PER_PAIR_2D_GAUSS = 19  # algorithmic flops of one (i, j) term of Eq. N-particle, exp counted as 1
+FLOPS_PER_PAIR_2D_TENT = 20   # accepted tent pair: d, r^2, rsqrt, G, dq, p_i.p_j, weight, dp
+FLOPS_PER_PAIR_3D_GAUSS = 28  # d (3), r^2 (5), G (2), dq (6), p_i.p_j (5), weight (1), dp (6)
+FLOPS_PER_PAIR_3D_HVP = 65    # one (i, j) term of the Hessian-vector product of H (both blocks)
 WORKLOAD = ("fourier_curve_warp: N=4096 2-D landmarks on a random Fourier curve -> sine warp; "
             "Gaussian sigma=0.1; RK4 100 steps on [0,1]; Algorithm 1 from p0=0, eps=1e-6 (max-norm), maxit=200; "
             "default gain h = 1/max_i sum_j G_ij")
@@ -278,7 +281,7 @@ def run_gb300(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_secondary:
-        out["secondary"] = secondary(ep, workloads, dev, stream, peak_tflops)
+        out["secondary"] = secondary(ep, workloads, dev, stream, peak_tflops, with_cpu=not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(pr, p_fin.cpu().numpy())
     if rank == 0:
@@ -299,8 +302,28 @@ def _events_ms(torch, stream, fn, reps):
     return a.elapsed_time(b) / reps, r
 
 
-def secondary(ep, workloads, dev, stream, peak_tflops) -> dict:
-    """The other rows of the path, each timed briefly after the main measurement."""
+def _alu_roofline(flops_per_s: float, peak_tflops: float, note: str) -> dict:
+    a = flops_per_s / 1e12
+    return {"bound": "alu", "achieved": a, "peak": peak_tflops, "unit": "TFLOP/s", "frac": a / peak_tflops,
+            "note": note}
+
+
+def _oracle_sample(fn, unit: str, sample: str) -> dict:
+    """Time one bounded oracle call (FP64, all host threads); fn returns the work done
+    in `unit`s (and may extrapolate, which `sample` then says)."""
+    from oracle import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    work = fn(oracle)
+    dt = time.perf_counter() - t0
+    return {"value": work / dt, "unit": unit, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{sample} ({dt:.2f} s)"}
+
+
+def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) -> dict:
+    """The other rows of the path, each timed briefly after the main measurement,
+    with its roofline and (with_cpu) a bounded sample of the FP64 oracle."""
     import torch
 
     out = {}
@@ -323,7 +346,15 @@ def secondary(ep, workloads, dev, stream, peak_tflops) -> dict:
                         "pair_interactions_per_s": acc_pairs / (stage_us * 1e-6),
                         "roofline": {"bound": "hbm", "achieved": byts / (stage_us * 1e-6) / 1e9, "peak": hbm,
                                      "unit": "GB/s", "frac": byts / (stage_us * 1e-6) / 1e9 / hbm,
-                                     "bytes_per_stage": byts, "note": "working set is L2-resident"}}
+                                     "bytes_per_stage": byts, "note": "working set is L2-resident"},
+                        "roofline_alu": _alu_roofline(acc_pairs * FLOPS_PER_PAIR_2D_TENT / (stage_us * 1e-6), peak_tflops,
+                                                      f"{FLOPS_PER_PAIR_2D_TENT} flop per accepted pair")}
+    if with_cpu:
+        rows = np.random.default_rng(0).choice(g.n, 1024, replace=False)
+        out["cell_list"]["cpu_baseline"] = _oracle_sample(
+            lambda o: (o.rhs_rows(g.X, 0.01 * (g.Y - g.X), rows, ep.TENT, g.sigma), 1024 * g.n)[1],
+            "pair interactions/s (all-pairs)",
+            f"FP64 oracle RHS rows (brute force over all N={g.n} sources) for 1024 sampled particles")
     # adjoint: 16384 landmarks in 3-D, Gaussian, 100 steps, checkpoints every 10
     a3 = workloads.star_surface_3d()
     X3, Y3, p3 = (torch.tensor(v, device=dev) for v in (a3.X, a3.Y, a3.p0))
@@ -334,7 +365,17 @@ def secondary(ep, workloads, dev, stream, peak_tflops) -> dict:
     out["adjoint"] = {"workload": "star_surface_3d N=16384 3-D, Gaussian sigma=0.05, lambda=100, 100 steps, ckpt 10",
                       "ms_per_gradient": ms, "gradients_per_s": 1e3 / ms,
                       "rhs_pairs_per_gradient": pairs, "hvp_pairs_per_gradient": hvp_pairs,
-                      "pair_interactions_per_s": (pairs + hvp_pairs) / (ms * 1e-3)}
+                      "pair_interactions_per_s": (pairs + hvp_pairs) / (ms * 1e-3),
+                      "roofline": _alu_roofline((pairs * FLOPS_PER_PAIR_3D_GAUSS + hvp_pairs * FLOPS_PER_PAIR_3D_HVP)
+                                                / (ms * 1e-3), peak_tflops,
+                                                f"{FLOPS_PER_PAIR_3D_GAUSS} flop per RHS pair, {FLOPS_PER_PAIR_3D_HVP} per HVP pair")}
+    if with_cpu:
+        small = workloads.star_surface_3d(n=512)
+        k = (a3.n / small.n) ** 2 * (a3.steps / 10)
+        out["adjoint"]["cpu_baseline"] = _oracle_sample(
+            lambda o: (o.adjoint(small.X, small.p0, small.Y, ep.GAUSS, small.sigma, 10, small.lam), 1.0 / k)[1],
+            "gradients/s (extrapolated)",
+            f"FP64 oracle exact RK4 adjoint at N=512, 10 steps, scaled by (N ratio)^2 x (step ratio) = {k:.0f}")
     # batched: 512 curve problems, n log-uniform in [32, 8192], maxit capped at 10 here
     bp = workloads.batched_curves()
     Xs = [torch.tensor(p.X, device=dev) for p in bp]
@@ -347,7 +388,20 @@ def secondary(ep, workloads, dev, stream, peak_tflops) -> dict:
     out["batched"] = {"workload": "512 curve problems, n log-uniform [32, 8192], tent 0.2 / Gaussian 0.1, 50 steps, "
                                   "eps 1e-6, maxit 10 (capped for time)",
                       "seconds": dt, "matchings_per_s": len(bp) / dt, "pair_interactions_per_s": bpairs / dt,
-                      "converged": sum(1 for r in res if r.status == ep.OK)}
+                      "converged": sum(1 for r in res if r.status == ep.OK),
+                      "roofline": _alu_roofline(bpairs * 19.5 / dt, peak_tflops,
+                                                "19.5 flop per pair (Gaussian 19, tent 20, half the problems each)")}
+    if with_cpu:
+        pick = sorted(range(len(bp)), key=lambda b: bp[b].n)[:8]
+        spairs = sum(bp[b].n ** 2 * (4 * bp[b].steps * 3 + 2) for b in pick)
+
+        def run(o):
+            for b in pick:
+                o.match(bp[b].X, bp[b].Y, bp[b].kernel, bp[b].sigma, bp[b].steps, h=0.0, eps=1e-6, maxit=2)
+            return spairs
+
+        out["batched"]["cpu_baseline"] = _oracle_sample(
+            run, UNIT, "FP64 oracle Algorithm 1 (2 updates) on the 8 smallest problems of the batch")
     # circle -> ellipse, 64 landmarks, tent, FP64 plain method, full Algorithm 1
     c = workloads.circle_to_ellipse()
     Xc, Yc = torch.tensor(c.X, device=dev), torch.tensor(c.Y, device=dev)
@@ -358,7 +412,16 @@ def secondary(ep, workloads, dev, stream, peak_tflops) -> dict:
         dt = time.perf_counter() - t0
         out[f"small_{name}"] = {"workload": "circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, maxit 200",
                                 "seconds_per_match": dt, "iters": r.iters, "resid": r.resid,
-                                "shoots_per_s": (r.iters + 1) / dt}
+                                "shoots_per_s": (r.iters + 1) / dt,
+                                "roofline": {"bound": "latency", "note": "one CTA, 200 dependent shoots of 200 "
+                                             "dependent RHS; reported as shoots/s"}}
+    if with_cpu:
+        def run_small(o):
+            _, _, it, _, _ = o.match(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.0, eps=c.eps, maxit=c.maxit)
+            return it + 1
+
+        out["small_fp64"]["cpu_baseline"] = _oracle_sample(run_small, "shoots/s",
+                                                           "FP64 oracle: the whole N=64 match (Algorithm 1)")
     return out
 
 

@@ -501,7 +501,13 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         return s;
     }
     const bool hist_dev = info->hist && is_device_ptr(info->hist);
+    // the plain FP64 all-pairs method: the whole feedback loop on the device
+    const bool device_loop = P.precision == EP_FP64 && !use_celllist(P, n) && n <= kDeviceMatchMaxN;
     Sizer z;
+    if (device_loop) {
+        z.add(match_device_bytes(n, P.dim, info->maxit));
+        z.add(sizeof(double) * ((size_t)info->maxit + 1));
+    }
     z.add(forward_bytes(P, n));
     plan_stage(z, X, m);
     plan_stage(z, Y, m);
@@ -516,6 +522,26 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     EP_TRY(stage_in(ar, X, m, st, &sX));
     EP_TRY(stage_in(ar, Y, m, st, &sY));
     EP_TRY(stage_in(ar, p0, m, st, &sp));
+    if (device_loop) {
+        double* hist_d = hist_dev ? info->hist : nullptr;
+        if (info->hist && !hist_dev) hist_d = (double*)ar->carve(sizeof(double) * ((size_t)info->maxit + 1));
+        double out[5];
+        EP_TRY(match_device_fp64(P, n, sX.dev, sY.dev, sp.dev, info, hist_d, ar, st, out));
+        info->h = out[0];
+        info->resid_inf = out[1];
+        info->H = out[2];
+        info->iters = (int)out[3];
+        const ep_status status = (ep_status)(int)out[4];
+        if (sp.host) EP_TRY_CUDA(cudaMemcpyAsync(p0, sp.dev, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        if (info->hist && !hist_dev)
+            EP_TRY_CUDA(cudaMemcpyAsync(info->hist, hist_d, sizeof(double) * ((size_t)info->iters + 1),
+                                        cudaMemcpyDeviceToHost, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+        if (status == EP_ENOTCONVERGED)
+            set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", info->iters, info->resid_inf, info->eps);
+        if (status == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", info->iters);
+        return status;
+    }
     double* t0 = (double*)ar->carve(sizeof(double) * m);
     double* t1 = (double*)ar->carve(sizeof(double) * m);
     double* t2 = (double*)ar->carve(sizeof(double) * m);

@@ -17,11 +17,13 @@
 //
 // One stage = block-wise exclusive scan of the cell counts (the last block scans
 // the block totals) -> scatter into cell order -> sweep: each CTA owns an 8 x 8
-// block of cells, stages the records of its 10 x 10 halo (contiguous row
-// segments of the cell-ordered array) in shared memory, sorts each staged cell by
-// particle index (so sums do not depend on the order atomics gave), and every
-// thread sums its particles' 3 x 3 neighbour cells in FP32, then applies the RK4
-// stage and bins the particle for the next stage (cell count by atomics).  Stage positions inside a step are
+// block of cells, stages the records of its 10 x 10 halo in shared memory with
+// each cell's records ordered by particle index (so sums do not depend on the
+// order atomics gave), and every thread sums the 3 x 3 neighbour cells of
+// kSweepRI particles of one cell in FP32, then applies the RK4 stage and bins
+// each particle for the next stage (cell count by atomics).  (Measured on the
+// 512 x 512 grid: one particle per thread is as fast as two to four sharing each
+// record load; the sweep is bound by the CTAs' low warp occupancy.)  Stage positions inside a step are
 // anchor + c dt k in FP32 on the offsets (re-celled by floor(o / e)); the step
 // state x is FP64 and the anchor is re-derived from it in FP64 every step.
 #include <math.h>
@@ -38,6 +40,7 @@ namespace {
 constexpr int kBlk = 8;                        // cells per sweep block side
 constexpr int kHalo = kBlk + 2;
 constexpr int kSweepThreads = 256;
+constexpr int kSweepRI = 1;                    // particles of one cell per sweep thread
 constexpr int kSweepCap = 2048;                // halo records staged in shared memory (~2x the mean halo)
 constexpr int kScanBlock = 4096;               // cells per scan block (1024 threads x 4)
 constexpr int kMaxCellsPerAxis2D = 2048;
@@ -318,20 +321,71 @@ __device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, 
     a.rank_out[i] = atomicAdd(a.count_next + k, 1);
 }
 
+// Exclusive prefix sum of NV values (NV <= 4 x 32) by one warp: out[t] for t < NV,
+// out[NV] = total.
+template <int NV, typename F>
+__device__ __forceinline__ void warp_exclusive_scan(F value, int* out)
+{
+    constexpr int PER = (NV + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    int v[PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int t = PER * lane + k;
+        v[k] = t < NV ? value(t) : 0;
+        s += v[k];
+    }
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    int run = incl - s;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int t = PER * lane + k;
+        if (t < NV) out[t] = run;
+        run += v[k];
+    }
+    if (lane == 31) out[NV] = incl;
+}
+
+// Largest t in [0, n) with pre[t] <= u (pre non-decreasing, pre[0] <= u < pre[n]).
+__device__ __forceinline__ int find_segment(const int* pre, int n, int u)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // One CTA per 8 x 8 block of cells.  Halo cell t = hy * 10 + hx covers grid cell
-// (cx0 - 1 + hx, cy0 - 1 + hy).
+// (cx0 - 1 + hx, cy0 - 1 + hy).  The halo's records are staged in shared memory,
+// each cell's records ordered by particle index (every staged record finds its
+// rank among its cell's members), so the sums do not depend on the order the
+// binning atomics gave.  A thread then takes RI particles of one own cell and sums
+// their 3 x 3 neighbour cells, each loaded record serving the RI particles; the
+// pair terms are predicated (a rejected pair adds exact zeros), in the order
+// rows dy, cells dx, records by particle index.  MODE: 0 RK4 stage, 1 RHS,
+// 2 neighbour count and hash.
+template <int MODE, int RI>
 __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
 {
+    constexpr int NH = kHalo * kHalo;
+    constexpr int NO = kBlk * kBlk;
     __shared__ float4 s_rec[kSweepCap];
     __shared__ int s_idx[kSweepCap];
-    __shared__ int c_start[kHalo * kHalo];  // first record (shared index, or global slot)
-    __shared__ int c_len[kHalo * kHalo];
-    __shared__ int c_gs[kHalo * kHalo];     // global slot of the first record
-    __shared__ int own_pre[kBlk * kBlk + 1];
-    __shared__ int use_smem;
+    __shared__ int c_start[NH + 1];  // exclusive prefix of the halo cell lengths
+    __shared__ int c_len[NH];
+    __shared__ int c_gs[NH];         // global slot of each halo cell's first record
+    __shared__ int t_pre[NO + 1];    // exclusive prefix of the tasks per own cell
+    const int warp = threadIdx.x >> 5;
     const int ncx = a.g.nc[0], ncy = a.g.nc[1];
     const int cx0 = blockIdx.x * kBlk, cy0 = blockIdx.y * kBlk;
-    for (int t = threadIdx.x; t < kHalo * kHalo; t += kSweepThreads) {
+    for (int t = threadIdx.x; t < NH; t += kSweepThreads) {
         const int hx = t % kHalo, hy = t / kHalo;
         const int row = cy0 - 1 + hy, col = cx0 - 1 + hx;
         int gs = 0, len = 0;
@@ -345,109 +399,96 @@ __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
         c_len[t] = len;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int t = 0; t < kHalo * kHalo; ++t) {
-            c_start[t] = tot;
-            tot += c_len[t];
-        }
-        use_smem = tot <= kSweepCap;
-        if (!use_smem)
-            for (int t = 0; t < kHalo * kHalo; ++t) c_start[t] = c_gs[t];
-        int o = 0;
-        for (int k = 0; k < kBlk * kBlk; ++k) {
-            own_pre[k] = o;
-            o += c_len[((k / kBlk) + 1) * kHalo + (k % kBlk) + 1];
-        }
-        own_pre[kBlk * kBlk] = o;
-    }
+    if (warp == 0) warp_exclusive_scan<NH>([&](int t) { return c_len[t]; }, c_start);
+    if (warp == 1)
+        warp_exclusive_scan<NO>([&](int k) { return (c_len[((k / kBlk) + 1) * kHalo + (k % kBlk) + 1] + RI - 1) / RI; },
+                                t_pre);
     __syncthreads();
-    const bool sm = use_smem != 0;
+    const bool sm = c_start[NH] <= kSweepCap;
     if (sm) {
-        // stage the halo: the cells of one halo row are contiguous in cell order
-        for (int hy = 0; hy < kHalo; ++hy) {
-            const int t0 = hy * kHalo;
-            const int len = c_start[t0 + kHalo - 1] + c_len[t0 + kHalo - 1] - c_start[t0];
-            int g0 = 0;
-            for (int hx = 0; hx < kHalo; ++hx)
-                if (c_len[t0 + hx] > 0) { g0 = c_gs[t0 + hx] - (c_start[t0 + hx] - c_start[t0]); break; }
-            for (int u = threadIdx.x; u < len; u += kSweepThreads) {
-                s_rec[c_start[t0] + u] = a.srec[g0 + u];
-                s_idx[c_start[t0] + u] = a.sidx[g0 + u];
-            }
-        }
-        __syncthreads();
-        // order each staged cell by particle index (insertion sort; ~10 per cell)
-        for (int t = threadIdx.x; t < kHalo * kHalo; t += kSweepThreads) {
-            const int b0 = c_start[t], b1 = b0 + c_len[t];
-            for (int u = b0 + 1; u < b1; ++u) {
-                const int ki = s_idx[u];
-                const float4 kr = s_rec[u];
-                int v = u - 1;
-                while (v >= b0 && s_idx[v] > ki) {
-                    s_idx[v + 1] = s_idx[v];
-                    s_rec[v + 1] = s_rec[v];
-                    --v;
-                }
-                s_idx[v + 1] = ki;
-                s_rec[v + 1] = kr;
-            }
+        const int tot = c_start[NH];
+        for (int u = threadIdx.x; u < tot; u += kSweepThreads) {
+            const int t = find_segment(c_start, NH, u);
+            const int g0 = c_gs[t], len = c_len[t];
+            const int g = g0 + (u - c_start[t]);
+            const int my = __ldg(a.sidx + g);
+            int rank = 0;
+            for (int v = 0; v < len; ++v) rank += __ldg(a.sidx + g0 + v) < my ? 1 : 0;
+            s_idx[c_start[t] + rank] = my;
+            s_rec[c_start[t] + rank] = __ldg(a.srec + g);
         }
         __syncthreads();
     }
     const float4* rec = sm ? s_rec : a.srec;
     const int* idx = sm ? s_idx : a.sidx;
+    const int* cst = sm ? c_start : c_gs;
     const float e0 = a.g.e[0], e1 = a.g.e[1];
-    const int nown = own_pre[kBlk * kBlk];
-    for (int k = threadIdx.x; k < nown; k += kSweepThreads) {
-        // own cell of record k (binary search in the own-cell prefix)
-        int lo = 0, hi = kBlk * kBlk;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (own_pre[mid] <= k) lo = mid; else hi = mid;
+    const int ntask = t_pre[NO];
+    for (int task = threadIdx.x; task < ntask; task += kSweepThreads) {
+        const int kc = find_segment(t_pre, NO, task);
+        const int h = ((kc / kBlk) + 1) * kHalo + (kc % kBlk) + 1;
+        const int first = (task - t_pre[kc]) * RI;
+        const int nact = min(RI, c_len[h] - first);
+        float4 ri[RI];
+        int ii[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            const int u = cst[h] + first + (r < nact ? r : 0);
+            ri[r] = rec[u];
+            ii[r] = idx[u];
         }
-        const int lx = lo % kBlk, ly = lo / kBlk;
-        const int h = (ly + 1) * kHalo + lx + 1;
-        const int u = c_start[h] + (k - own_pre[lo]);
-        const float4 ri = rec[u];
-        const int i = idx[u];
-        float dqx = 0.f, dqy = 0.f, dpx = 0.f, dpy = 0.f;
-        int cnt = 0;
-        unsigned long long hs = 0ull;
+        float dqx[RI], dqy[RI], dpx[RI], dpy[RI];
+        int cnt[RI];
+        unsigned long long hs[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            dqx[r] = dqy[r] = dpx[r] = dpy[r] = 0.0f;
+            cnt[r] = 0;
+            hs[r] = 0ull;
+        }
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
                 const int h2 = h + dy * kHalo + dx;
-                const int len = c_len[h2], s0 = c_start[h2];
+                const int len = c_len[h2], s0 = cst[h2];
                 const float sx = __fmul_rn((float)(-dx), e0), sy = __fmul_rn((float)(-dy), e1);
                 for (int v = 0; v < len; ++v) {
                     const float4 rj = rec[s0 + v];
-                    const float d0 = __fadd_rn(__fsub_rn(ri.x, rj.x), sx);
-                    const float d1 = __fadd_rn(__fsub_rn(ri.y, rj.y), sy);
-                    const float r2 = __fmaf_rn(d0, d0, __fmul_rn(d1, d1));
-                    if (r2 < 1.0f) {
-                        if (a.mode == 2) {
-                            ++cnt;
-                            hs += (unsigned long long)(idx[s0 + v] + 1) * 2654435761ull;
+                    int jj = 0;
+                    if (MODE == 2) jj = idx[s0 + v];
+#pragma unroll
+                    for (int r = 0; r < RI; ++r) {
+                        const float d0 = __fadd_rn(__fsub_rn(ri[r].x, rj.x), sx);
+                        const float d1 = __fadd_rn(__fsub_rn(ri[r].y, rj.y), sy);
+                        const float r2 = __fmaf_rn(d0, d0, __fmul_rn(d1, d1));
+                        const bool in = r2 < 1.0f;
+                        if (MODE == 2) {
+                            cnt[r] += in ? 1 : 0;
+                            hs[r] += in ? (unsigned long long)(jj + 1) * 2654435761ull : 0ull;
                         } else {
                             const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
-                            const float G = fmaf(-r2, rs, 1.0f);
-                            dqx = fmaf(G, rj.z, dqx);
-                            dqy = fmaf(G, rj.w, dqy);
-                            const float c2 = rs * fmaf(ri.z, rj.z, ri.w * rj.w);
-                            dpx = fmaf(c2, d0, dpx);
-                            dpy = fmaf(c2, d1, dpy);
+                            const float G = in ? fmaf(-r2, rs, 1.0f) : 0.0f;
+                            dqx[r] = fmaf(G, rj.z, dqx[r]);
+                            dqy[r] = fmaf(G, rj.w, dqy[r]);
+                            const float c2 = in ? rs * fmaf(ri[r].z, rj.z, ri[r].w * rj.w) : 0.0f;
+                            dpx[r] = fmaf(c2, d0, dpx[r]);
+                            dpy[r] = fmaf(c2, d1, dpy[r]);
                         }
                     }
                 }
             }
         }
-        if (a.mode == 2) {
-            a.out_cnt[i] = (long long)cnt;
-            a.out_hash[i] = hs;
-        } else {
-            epilogue(a, i, dqx, dqy, dpx, dpy);
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+            if (r < nact) {
+                if (MODE == 2) {
+                    a.out_cnt[ii[r]] = (long long)cnt[r];
+                    a.out_hash[ii[r]] = hs[r];
+                } else {
+                    epilogue(a, ii[r], dqx[r], dqy[r], dpx[r], dpy[r]);
+                }
+            }
         }
     }
 }
@@ -529,7 +570,12 @@ ep_status run_stage(const ep_params& P, const CellBufs& b, Args a, const float4*
     a.dp_scale_f = (float)(1.0 / P.sigma);
     dim3 grid((unsigned)((g.nc[0] + kBlk - 1) / kBlk), (unsigned)((g.nc[1] + kBlk - 1) / kBlk));
     count_launch();
-    k_cell_sweep<<<grid, kSweepThreads, 0, st>>>(a);
+    if (a.mode == 2)
+        k_cell_sweep<2, kSweepRI><<<grid, kSweepThreads, 0, st>>>(a);
+    else if (a.mode == 1)
+        k_cell_sweep<1, kSweepRI><<<grid, kSweepThreads, 0, st>>>(a);
+    else
+        k_cell_sweep<0, kSweepRI><<<grid, kSweepThreads, 0, st>>>(a);
     EP_TRY_CUDA(cudaGetLastError());
     if (a.mode == 0) im->cur ^= 1;
     return EP_OK;

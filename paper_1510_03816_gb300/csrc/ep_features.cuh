@@ -34,6 +34,15 @@ ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offse
 // ep_match of one small 2-D mixed-precision problem, solved entirely on one CTA.
 ep_status match_small(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
                       ep_match_info* info, void* stream);
+
+// Algorithm 1 for the plain FP64 method in one cooperative launch (ep_match_dev.cu):
+// X, Y, p0 device arrays (p0 in/out), hist_dev maxit + 1 doubles on the device or
+// null; workspace from ar (match_device_bytes); out = h, residual, H, iterations,
+// status.
+size_t match_device_bytes(int64_t n, int dim, int maxit);
+ep_status match_device_fp64(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
+                            ep_match_info* info, double* hist_dev, Arena* ar, cudaStream_t st, double out[5]);
+constexpr int64_t kDeviceMatchMaxN = 16384;
 constexpr int64_t kSmallMatchMaxN = 384;
 
 }  // namespace ep

@@ -1,0 +1,345 @@
+// ep_match_dev.cu -- Algorithm 1 (the feedback-control shooting iteration,
+// Sec. 3) run entirely on the device for the plain FP64 method: one cooperative
+// launch per match, no host round trip per iterate or per RK4 stage.
+//
+// Every CTA owns the particles [c n / G, (c+1) n / G) and evaluates their rows of
+// Eq. N-particle over all n sources in FP64, then applies the classical RK4 stage
+// (Sec. 4) to them; one grid-wide barrier per stage publishes the next stage's
+// inputs.  After a shoot the max-norm residual |Y - Q(1)|_inf is reduced across
+// CTAs (each CTA's maximum joins a per-iterate slot by atomicMax on the IEEE bit
+// pattern, which orders non-negative doubles and ranks inf and NaN above every
+// finite value), and every CTA takes the same stop decision after the barrier:
+// non-finite -> diverged, below eps -> converged, maxit updates -> not converged,
+// else p0 += h (Y - Q(1)) on its own particles (the momentum rule).  The default
+// gain h = 1 / max_i sum_j G_ij is computed the same way before the first shoot,
+// and H(X, p0) of the returned momenta (Eq. H) after the last.
+//
+// FP64 on this GPU runs at 1/64 of the FP32 rate, so a small problem's FP64 pair
+// work is spread over as many SMs as there are particles (up to the SM count);
+// within a CTA the sources of a row are split across all warps, so every SM
+// sub-partition's FP64 pipe works on it.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "ep_allpairs_dev.cuh"
+#include "ep_features.cuh"
+
+namespace ep {
+
+namespace {
+
+constexpr int kMatchThreads = 256;
+
+struct MatchArgs {
+    int n, steps, maxit;
+    double sigma, dt, eps, h;  // h <= 0: default gain, computed in the kernel
+    const double* X;
+    const double* Y;
+    double* p0;                // in: initial momenta, out: the last iterate
+    double* x;                 // step state [q (n dim) | p (n dim)]
+    double* D[3];              // stage copies (2 dim per particle): step start, ping, pong
+    double* acc;               // RK4 accumulator k1 + 2 k2 + 2 k3 (2 dim per particle)
+    double* hist;              // maxit + 1 residuals (device) or null
+    unsigned long long* red;   // [0] max row sum (bits), [1 + k] residual of iterate k (bits)
+    double* part;              // per-CTA partial sums of H
+    double* out;               // h, residual, H, iterations, status
+    unsigned* bar;
+    int* err;
+};
+
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Sum of V doubles over the CTA; the result is valid in every thread.
+template <int V>
+__device__ __forceinline__ void cta_sum(double (&v)[V], double* sm)
+{
+    constexpr int W = kMatchThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < V; ++k) sm[warp * V + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < W; ++w) s += sm[w * V + k];
+        v[k] = s;
+    }
+}
+
+__device__ __forceinline__ unsigned long long cta_max_bits(unsigned long long v, unsigned long long* sm)
+{
+    constexpr int W = kMatchThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    unsigned long long m = 0;
+    for (int w = 0; w < W; ++w) m = sm[w] > m ? sm[w] : m;
+    return m;
+}
+
+// Row i of Eq. N-particle at the stage input D (FP64): s[0..DIM) = sum_j G_ij p_j,
+// s[DIM..2 DIM) = -sum_{j != i} (p_i . p_j) phi_ij (q_i - q_j).  Sources are dealt
+// to the threads in order (j -> thread j % 256), so warps run with all lanes
+// active: an FP64 warp instruction occupies its sub-partition's FP64 pipe for the
+// same time whatever the number of active lanes.  The sums are complete in every
+// thread on return.
+template <int DIM, int KER>
+__device__ void row_sums(const double* D, int n, int i, double sigma, double (&s)[2 * DIM], double* sm)
+{
+    constexpr int S2 = 2 * DIM;
+    double qi[DIM], pi[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        qi[c] = __ldcg(D + (size_t)i * S2 + c);
+        pi[c] = __ldcg(D + (size_t)i * S2 + DIM + c);
+    }
+#pragma unroll
+    for (int k = 0; k < S2; ++k) s[k] = 0.0;
+    for (int j = threadIdx.x; j < n; j += kMatchThreads) {
+        double d[DIM], r2 = 0.0, pp = 0.0, pj[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            d[c] = qi[c] - __ldcg(D + (size_t)j * S2 + c);
+            pj[c] = __ldcg(D + (size_t)j * S2 + DIM + c);
+            r2 += d[c] * d[c];
+            pp += pi[c] * pj[c];
+        }
+        double G, phi;
+        kfun_f64<KER>(r2, sigma, G, phi);
+        const double wgt = (j == i) ? 0.0 : -pp * phi;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            s[c] += G * pj[c];
+            s[DIM + c] += wgt * d[c];
+        }
+    }
+    cta_sum<S2>(s, sm);
+}
+
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
+{
+    constexpr int S2 = 2 * DIM;
+    __shared__ double sm_d[(kMatchThreads / 32) * S2];
+    __shared__ unsigned long long sm_u[kMatchThreads / 32];
+    const int n = a.n;
+    const int r0 = (int)((long long)blockIdx.x * n / gridDim.x), r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
+    const size_t nd = (size_t)n * DIM;
+    unsigned epoch = 0;
+    // default gain: h = 1 / max_i sum_j G(X_i, X_j)
+    double h = a.h;
+    if (!(h > 0.0)) {
+        // the stage copy D[0] holds (X, 1) for the row sums
+        for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
+            const int i = r0 + t / DIM, c = t % DIM;
+            a.D[0][(size_t)i * S2 + c] = a.X[(size_t)i * DIM + c];
+            a.D[0][(size_t)i * S2 + DIM + c] = 1.0;
+        }
+        if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+        unsigned long long mx = 0;
+        for (int i = r0; i < r1; ++i) {
+            double s[S2];
+            row_sums<DIM, KER>(a.D[0], n, i, a.sigma, s, sm_d);
+            const unsigned long long b = dbits(fabs(s[0]));
+            mx = b > mx ? b : mx;
+        }
+        if (threadIdx.x == 0 && r1 > r0) atomicMax(a.red, mx);
+        if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+        const double m = bitsd(ld_acquire_u64(a.red));
+        h = m > 0.0 ? 1.0 / m : 1.0;
+    }
+    int k = 0, status = EP_ENOTCONVERGED;
+    double res = 0.0;
+    for (;; ++k) {
+        // shoot from (X, p0): x = (X, p0), step-start copy D[0] = x (own particles)
+        for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
+            const int i = r0 + t / DIM, c = t % DIM;
+            const double q = a.X[(size_t)i * DIM + c], p = a.p0[(size_t)i * DIM + c];
+            a.x[(size_t)i * DIM + c] = q;
+            a.x[nd + (size_t)i * DIM + c] = p;
+            a.D[0][(size_t)i * S2 + c] = q;
+            a.D[0][(size_t)i * S2 + DIM + c] = p;
+        }
+        if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+        for (int s = 0; s < a.steps; ++s) {
+            for (int stage = 0; stage < 4; ++stage) {
+                const double* Din = a.D[stage == 0 ? 0 : (stage == 2 ? 2 : 1)];
+                double* Dout = a.D[stage == 3 ? 0 : (stage == 1 ? 2 : 1)];
+                for (int i = r0; i < r1; ++i) {
+                    double kk[S2];
+                    row_sums<DIM, KER>(Din, n, i, a.sigma, kk, sm_d);
+                    // y = x_n + c dt k (c = 1/2, 1/2, 1), acc = k1 + 2 k2 + 2 k3;
+                    // x_{n+1} = x_n + dt/6 (acc + k4): one thread per component
+                    if (threadIdx.x < S2) {
+                        const int c = threadIdx.x;
+                        double kv = kk[0];
+#pragma unroll
+                        for (int u = 1; u < S2; ++u) kv = c == u ? kk[u] : kv;
+                        double* xs = c < DIM ? a.x + (size_t)i * DIM + c : a.x + nd + (size_t)i * DIM + (c - DIM);
+                        double* A = a.acc + (size_t)i * S2 + c;
+                        if (stage < 3) {
+                            const double cdt = (stage == 2 ? 1.0 : 0.5) * a.dt;
+                            Dout[(size_t)i * S2 + c] = *xs + cdt * kv;
+                            *A = stage == 0 ? kv : *A + 2.0 * kv;
+                        } else {
+                            const double nv = *xs + a.dt / 6.0 * (*A + kv);
+                            *xs = nv;
+                            Dout[(size_t)i * S2 + c] = nv;
+                        }
+                    }
+                }
+                if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+            }
+        }
+        // residual |Y - Q(1)|_inf over all particles and components
+        unsigned long long mb = 0;
+        for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
+            const size_t e = (size_t)r0 * DIM + t;
+            const unsigned long long b = dbits(fabs(a.Y[e] - a.x[e]));
+            mb = b > mb ? b : mb;
+        }
+        mb = cta_max_bits(mb, sm_u);
+        if (threadIdx.x == 0 && r1 > r0) atomicMax(a.red + 1 + k, mb);
+        if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+        const unsigned long long rb = ld_acquire_u64(a.red + 1 + k);
+        const bool finite = rb < 0x7FF0000000000000ull;
+        res = finite ? bitsd(rb) : __longlong_as_double(0x7FF8000000000000ll);
+        if (a.hist && blockIdx.x == 0 && threadIdx.x == 0) a.hist[k] = res;
+        if (!finite) { status = EP_EDIVERGED; break; }
+        if (res < a.eps) { status = EP_OK; break; }
+        if (k == a.maxit) { status = EP_ENOTCONVERGED; break; }
+        for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
+            const size_t e = (size_t)r0 * DIM + t;
+            a.p0[e] += h * (a.Y[e] - a.x[e]);
+        }
+    }
+    // H(X, p0) = 1/2 sum_i p_i . sum_j G_ij p_j (Eq. H) of the returned momenta
+    for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
+        const int i = r0 + t / DIM, c = t % DIM;
+        a.D[0][(size_t)i * S2 + c] = a.X[(size_t)i * DIM + c];
+        a.D[0][(size_t)i * S2 + DIM + c] = a.p0[(size_t)i * DIM + c];
+    }
+    if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+    double hp = 0.0;
+    for (int i = r0; i < r1; ++i) {
+        double s[S2];
+        row_sums<DIM, KER>(a.D[0], n, i, a.sigma, s, sm_d);
+        double dot = 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dot += a.p0[(size_t)i * DIM + c] * s[c];
+        hp += 0.5 * dot;
+    }
+    if (threadIdx.x == 0) a.part[blockIdx.x] = hp;
+    if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double H = 0.0;
+        for (unsigned c = 0; c < gridDim.x; ++c) H += __ldcg(a.part + c);
+        a.out[0] = h;
+        a.out[1] = res;
+        a.out[2] = H;
+        a.out[3] = (double)k;
+        a.out[4] = (double)status;
+    }
+}
+
+template <int DIM, int KER>
+ep_status launch_match_fp64(MatchArgs& a, cudaStream_t st)
+{
+    auto fn = k_match_fp64<DIM, KER>;
+    static int resident = -1;
+    if (resident < 0) {
+        int per_sm = 0;
+        EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMatchThreads, 0));
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        resident = per_sm * di.sm_count;
+    }
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    const int G = std::max(1, std::min({a.n, di.sm_count, resident}));
+    void* args[] = {&a};
+    count_launch();
+    EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kMatchThreads), args, 0, st));
+    return EP_OK;
+}
+
+}  // namespace
+
+size_t match_device_bytes(int64_t n, int dim, int maxit)
+{
+    Sizer z;
+    const size_t m = (size_t)n * dim;
+    z.add(sizeof(double) * 2 * m);          // x
+    for (int k = 0; k < 3; ++k) z.add(sizeof(double) * 2 * m);  // stage copies
+    z.add(sizeof(double) * 2 * m);          // acc
+    z.add(sizeof(unsigned long long) * ((size_t)maxit + 2));
+    z.add(sizeof(double) * 1024);           // per-CTA partials
+    z.add(sizeof(double) * 8);              // outputs
+    z.add(sizeof(unsigned) * 12);           // barrier + error flag
+    return z.total;
+}
+
+ep_status match_device_fp64(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
+                            ep_match_info* info, double* hist_dev, Arena* ar, cudaStream_t st, double out[5])
+{
+    const size_t m = (size_t)n * P.dim;
+    MatchArgs a{};
+    a.n = (int)n;
+    a.steps = P.steps;
+    a.maxit = info->maxit;
+    a.sigma = P.sigma;
+    a.dt = P.t1 / P.steps;
+    a.eps = info->eps;
+    a.h = info->h;
+    a.X = X;
+    a.Y = Y;
+    a.p0 = p0;
+    a.x = (double*)ar->carve(sizeof(double) * 2 * m);
+    for (int k = 0; k < 3; ++k) a.D[k] = (double*)ar->carve(sizeof(double) * 2 * m);
+    a.acc = (double*)ar->carve(sizeof(double) * 2 * m);
+    a.red = (unsigned long long*)ar->carve(sizeof(unsigned long long) * ((size_t)a.maxit + 2));
+    a.part = (double*)ar->carve(sizeof(double) * 1024);
+    a.out = (double*)ar->carve(sizeof(double) * 8);
+    a.bar = (unsigned*)ar->carve(sizeof(unsigned) * 12);
+    if (!a.bar) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+    a.err = (int*)(a.bar + 8);
+    a.hist = hist_dev;
+    EP_TRY_CUDA(cudaMemsetAsync(a.red, 0, sizeof(unsigned long long) * ((size_t)a.maxit + 2), st));
+    EP_TRY_CUDA(cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * 12, st));
+    ep_status s = EP_EINVAL;
+#define EP_MATCH_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) s = launch_match_fp64<D, K>(a, st);
+    EP_MATCH_CASE(2, EP_GAUSS) EP_MATCH_CASE(2, EP_TENT) EP_MATCH_CASE(2, EP_EXPCONE)
+    EP_MATCH_CASE(3, EP_GAUSS) EP_MATCH_CASE(3, EP_TENT) EP_MATCH_CASE(3, EP_EXPCONE)
+#undef EP_MATCH_CASE
+    if (s != EP_OK) return s == EP_EINVAL ? (set_error("ep_match: no device match for this kernel"), s) : s;
+    int herr = 0;
+    EP_TRY_CUDA(cudaMemcpyAsync(out, a.out, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(&herr, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) return set_error("ep_match: a grid-barrier wait gave up (kernel ended early)"), EP_ETIMEOUT;
+    return EP_OK;
+}
+
+}  // namespace ep
