@@ -20,7 +20,10 @@
  *   - Hessian-vector product of H and the exact discrete adjoint of the RK4
  *     shoot for the inexact-matching energy               (Sec. 6, Eq. inexact-E)
  *   - brute-force neighbour sets of the cell-list predicate (a written
- *     definition of the GPU path's FP32 acceptance test; see orc_cell_*).
+ *     definition of the GPU path's FP32 acceptance test; see orc_cell_*)
+ *   - the velocity field at arbitrary points             (Sec. 3.1, Eq. u)
+ *     and the transport of points by the flow it generates along a shoot
+ *     (the deformation phi_t with d phi_t(x)/dt = u(phi_t(x), t)).
  *
  * Parity pins (tests/test_oracle_pins.py): every function here is checked
  * against something other than itself -- finite differences of H, closed
@@ -222,6 +225,75 @@ int orc_shoot(int dim, int kernel, double sigma, int steps, double t1, long n, c
     double dt = t1 / steps;
     for (int s = 0; s < steps; ++s) rk4_step(dim, kernel, sigma, n, dt, q1, p1, work);
     free(work);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. u: the velocity at m points x (m, dim) of the momenta p carried by    */
+/* the particles q (n, dim):  u(x_k) = sum_{j=1..N} G(|x_k - q_j|) p_j.       */
+/* ------------------------------------------------------------------------ */
+void orc_velocity(int dim, int kernel, double sigma, long n, const double* q, const double* p, long m,
+                  const double* x, double* u)
+{
+    long k;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k < m; ++k) {
+        const double* xk = x + k * dim;
+        double s[3] = {0.0, 0.0, 0.0};
+        for (long j = 0; j < n; ++j) {
+            double g = orc_G(kernel, sigma, dist(dim, xk, q + j * dim));
+            for (int c = 0; c < dim; ++c) s[c] += g * p[j * dim + c];
+        }
+        for (int c = 0; c < dim; ++c) u[k * dim + c] = s[c];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transport of m points by the flow of a shoot: the joint system            */
+/*   dq/dt, dp/dt = Eq. N-particle,   dx_k/dt = u(x_k, t)  (Eq. u at q(t), p(t)) */
+/* integrated by the classical RK4 of the shoot (the same steps on [0, t1]), */
+/* so x1 = phi_{t1}(x0).  The particles' endpoint goes to q1, p1.            */
+/* ------------------------------------------------------------------------ */
+int orc_flow(int dim, int kernel, double sigma, int steps, double t1, long n, const double* q0,
+             const double* p0, long m, const double* x0, double* q1, double* p1, double* x1)
+{
+    if (dim < 1 || dim > 3 || steps < 1 || n < 0 || m < 0) return ORC_EINVAL;
+    long a, nd = n * dim, md = m * dim;
+    double* w = (double*)malloc(sizeof(double) * (size_t)(10 * nd + 5 * md + 1));
+    if (!w) return ORC_EINVAL;
+    double *k1q = w, *k1p = w + nd, *k2q = w + 2 * nd, *k2p = w + 3 * nd, *k3q = w + 4 * nd;
+    double *k3p = w + 5 * nd, *k4q = w + 6 * nd, *k4p = w + 7 * nd, *yq = w + 8 * nd, *yp = w + 9 * nd;
+    double *k1x = w + 10 * nd, *k2x = k1x + md, *k3x = k2x + md, *k4x = k3x + md, *yx = k4x + md;
+    memcpy(q1, q0, sizeof(double) * (size_t)nd);
+    memcpy(p1, p0, sizeof(double) * (size_t)nd);
+    memcpy(x1, x0, sizeof(double) * (size_t)md);
+    double dt = t1 / steps;
+    for (int s = 0; s < steps; ++s) {
+        /* stage 1 at (q, p, x) */
+        orc_rhs(dim, kernel, sigma, n, q1, p1, k1q, k1p);
+        orc_velocity(dim, kernel, sigma, n, q1, p1, m, x1, k1x);
+        /* stage 2 at the half step along k1 */
+        for (a = 0; a < nd; ++a) { yq[a] = q1[a] + 0.5 * dt * k1q[a]; yp[a] = p1[a] + 0.5 * dt * k1p[a]; }
+        for (a = 0; a < md; ++a) yx[a] = x1[a] + 0.5 * dt * k1x[a];
+        orc_rhs(dim, kernel, sigma, n, yq, yp, k2q, k2p);
+        orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k2x);
+        /* stage 3 at the half step along k2 */
+        for (a = 0; a < nd; ++a) { yq[a] = q1[a] + 0.5 * dt * k2q[a]; yp[a] = p1[a] + 0.5 * dt * k2p[a]; }
+        for (a = 0; a < md; ++a) yx[a] = x1[a] + 0.5 * dt * k2x[a];
+        orc_rhs(dim, kernel, sigma, n, yq, yp, k3q, k3p);
+        orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k3x);
+        /* stage 4 at the full step along k3 */
+        for (a = 0; a < nd; ++a) { yq[a] = q1[a] + dt * k3q[a]; yp[a] = p1[a] + dt * k3p[a]; }
+        for (a = 0; a < md; ++a) yx[a] = x1[a] + dt * k3x[a];
+        orc_rhs(dim, kernel, sigma, n, yq, yp, k4q, k4p);
+        orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k4x);
+        for (a = 0; a < nd; ++a) {
+            q1[a] += dt / 6.0 * (k1q[a] + 2.0 * k2q[a] + 2.0 * k3q[a] + k4q[a]);
+            p1[a] += dt / 6.0 * (k1p[a] + 2.0 * k2p[a] + 2.0 * k3p[a] + k4p[a]);
+        }
+        for (a = 0; a < md; ++a) x1[a] += dt / 6.0 * (k1x[a] + 2.0 * k2x[a] + 2.0 * k3x[a] + k4x[a]);
+    }
+    free(w);
     return ORC_OK;
 }
 

@@ -86,6 +86,10 @@ def _load():
         lib.orc_rhs_rows.argtypes = [i, i, d, l, p, p, p, l, p, p]
         lib.orc_cell_neighbors_rows.restype = None
         lib.orc_cell_neighbors_rows.argtypes = [i, d, l, p, p, l, p, p]
+        lib.orc_velocity.restype = None
+        lib.orc_velocity.argtypes = [i, i, d, l, p, p, l, p, p]
+        lib.orc_flow.restype = i
+        lib.orc_flow.argtypes = [i, i, d, i, d, l, p, p, l, p, p, p, p]
         lib.orc_set_threads.restype = None
         lib.orc_set_threads.argtypes = [i]
         lib.orc_max_threads.restype = i
@@ -264,3 +268,28 @@ def cell_neighbors_rows(q, rows, sigma: float):
     _load().orc_cell_neighbors_rows(dim, sigma, n, _ptr(q), rows.ctypes.data_as(ctypes.c_void_p), rows.size,
                                     cnt.ctypes.data_as(ctypes.c_void_p), hsh.ctypes.data_as(ctypes.c_void_p))
     return cnt, hsh
+
+
+def velocity(q, p, x, kernel: int, sigma: float):
+    """Eq. u: u(x_k) = sum_j G(|x_k - q_j|) p_j at the points x (m, dim)."""
+    q = _arr(q)
+    dim = q.shape[1]
+    p = _arr(p, dim)
+    x = _arr(x, dim)
+    u = np.empty_like(x)
+    _load().orc_velocity(dim, kernel, sigma, q.shape[0], _ptr(q), _ptr(p), x.shape[0], _ptr(x), _ptr(u))
+    return u
+
+
+def flow(q0, p0, x0, kernel: int, sigma: float, steps: int, t1: float = 1.0):
+    """Points x0 transported by the flow of the shoot from (q0, p0): returns (Q1, P1, X1)."""
+    q0 = _arr(q0)
+    dim = q0.shape[1]
+    p0 = _arr(p0, dim)
+    x0 = _arr(x0, dim)
+    q1, p1, x1 = np.empty_like(q0), np.empty_like(p0), np.empty_like(x0)
+    st = _load().orc_flow(dim, kernel, sigma, steps, t1, q0.shape[0], _ptr(q0), _ptr(p0), x0.shape[0], _ptr(x0),
+                          _ptr(q1), _ptr(p1), _ptr(x1))
+    if st != 0:
+        raise ValueError("orc_flow: invalid arguments")
+    return q1, p1, x1

@@ -36,6 +36,14 @@ MUTANTS = {
     "expcone_psi_term": ("(1.0 / (sigma * sigma * r * r) + 1.0 / (sigma * r * r * r))",
                          "(1.0 / (sigma * sigma * r * r))"),
     "cell_predicate_le": ("if (r2 < 1.0f) {", "if (r2 <= 1.1f) {"),
+    "velocity_uses_positions": ("for (int c = 0; c < dim; ++c) s[c] += g * p[j * dim + c];",
+                                "for (int c = 0; c < dim; ++c) s[c] += g * q[j * dim + c];"),
+    "flow_stage3_input": ("for (a = 0; a < md; ++a) yx[a] = x1[a] + 0.5 * dt * k2x[a];",
+                          "for (a = 0; a < md; ++a) yx[a] = x1[a] + 0.5 * dt * k1x[a];"),
+    "flow_weights": ("x1[a] += dt / 6.0 * (k1x[a] + 2.0 * k2x[a] + 2.0 * k3x[a] + k4x[a]);",
+                     "x1[a] += dt / 6.0 * (k1x[a] + 2.0 * k2x[a] + 1.0 * k3x[a] + 2.0 * k4x[a]);"),
+    "flow_stale_velocity_stage": ("orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k4x);",
+                                  "orc_velocity(dim, kernel, sigma, n, q1, p1, m, yx, k4x);"),
 }
 # mutations applied at every occurrence: these lines appear both in the full
 # function and in its row-sampled variant (orc_rhs_rows, orc_cell_neighbors_rows)

@@ -369,3 +369,83 @@ def test_row_sampled_variants_equal_the_full_sums():
     rc, rh = o.cell_neighbors_rows(q, rows, 0.06)
     np.testing.assert_array_equal(rc, cnt[rows])
     np.testing.assert_array_equal(rh, hsh[rows])
+
+
+# --------------------------------------------------------------------------- velocity field and flow (Eq. u)
+
+
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_velocity_is_the_probe_momentum_gradient_of_H(kernel, sigma, dim):
+    """Eq. u is dH/dv for a zero-momentum probe particle at x: with the probe's momentum v,
+    H = H(q, p) + sum_j (v . p_j) G(|x - q_j|) + |v|^2 G(0) / 2, whose central difference
+    in v at v = 0 is u(x) exactly (the quadratic term cancels)."""
+    q, p = _cloud(9, dim, seed=40 + dim + kernel, spread=0.8, pscale=0.3, min_gap=0.05, sigma=sigma, kernel=kernel)
+    x = np.random.default_rng(41).uniform(0, 0.8, size=(4, dim))
+    u = o.velocity(q, p, x, kernel, sigma)
+    eps = 1e-3
+    for k in range(x.shape[0]):
+        qa = np.vstack([q, x[k]])
+        for c in range(dim):
+            v = np.zeros((1, dim))
+            v[0, c] = eps
+            hp = o.hamiltonian(qa, np.vstack([p, v]), kernel, sigma)
+            hm = o.hamiltonian(qa, np.vstack([p, -v]), kernel, sigma)
+            assert abs((hp - hm) / (2 * eps) - u[k, c]) < 1e-10 * max(1.0, abs(u[k, c]))
+
+
+def test_velocity_at_the_particles_is_dq():
+    """Eq. u evaluated at q_i is the position rate of Eq. N-particle (self term included)."""
+    for kernel, sigma in KERNELS:
+        q, p = _cloud(14, 2, seed=43, spread=0.8, pscale=0.3, min_gap=0.02, sigma=sigma, kernel=kernel)
+        dq, _ = o.rhs(q, p, kernel, sigma)
+        np.testing.assert_allclose(o.velocity(q, p, q, kernel, sigma), dq, rtol=0, atol=1e-15)
+
+
+def test_flow_tracers_started_on_particles_follow_them():
+    """A point started at a particle obeys the same ODE as that particle's position, so
+    RK4 carries it exactly along: x1 = Q(1) of the plain shoot."""
+    for kernel, sigma in KERNELS:
+        q, p = _cloud(11, 2, seed=44, spread=0.7, pscale=0.2, min_gap=0.02, sigma=sigma, kernel=kernel)
+        x0 = q[[0, 3, 7]]
+        q1, p1, x1 = o.flow(q, p, x0, kernel, sigma, 13)
+        qs, ps = o.shoot(q, p, kernel, sigma, 13)
+        np.testing.assert_allclose(q1, qs, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(p1, ps, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(x1, qs[[0, 3, 7]], rtol=0, atol=1e-14)
+
+
+def test_flow_without_momentum_is_the_identity_and_reverses_in_time():
+    q, p = _cloud(10, 2, seed=45, spread=0.7, pscale=0.2, min_gap=0.02)
+    x0 = np.random.default_rng(46).uniform(0, 0.7, size=(25, 2))
+    _, _, x1 = o.flow(q, np.zeros_like(p), x0, o.GAUSS, 0.3, 5)
+    np.testing.assert_array_equal(x1, x0)
+    errs = []
+    for steps in (20, 40):
+        q1, p1, x1 = o.flow(q, p, x0, o.GAUSS, 0.3, steps, t1=1.0)
+        _, _, xb = o.flow(q1, p1, x1, o.GAUSS, 0.3, steps, t1=-1.0)
+        errs.append(np.abs(xb - x0).max())
+    assert errs[1] < 1e-8 and errs[0] / errs[1] > 10
+
+
+def test_flow_of_one_particle_matches_an_ode_solver_and_is_fourth_order():
+    """One Gaussian particle moves straight (q = q0 + p0 t, p = p0); points follow
+    dx/dt = G(|x - q(t)|) p0, solved here by an adaptive high-order integrator."""
+    sigma = 0.2
+    q0 = np.array([[0.3, 0.4]])
+    p0 = np.array([[0.15, 0.05]])
+    x0 = np.array([[0.35, 0.42], [0.1, 0.6], [0.5, 0.3]])
+
+    def f(t, y):
+        x = y.reshape(-1, 2)
+        qt = q0[0] + p0[0] * t
+        g = np.exp(-np.sum((x - qt) ** 2, axis=1) / (2 * sigma ** 2))
+        return (g[:, None] * p0[0]).ravel()
+
+    ref = solve_ivp(f, (0.0, 1.0), x0.ravel(), method="DOP853", rtol=1e-13, atol=1e-14).y[:, -1].reshape(-1, 2)
+    errs = []
+    for steps in (8, 16, 32):
+        _, _, x1 = o.flow(q0, p0, x0, o.GAUSS, sigma, steps)
+        errs.append(np.abs(x1 - ref).max())
+    assert errs[2] < 1e-8
+    assert 12.0 < errs[0] / errs[1] < 20.0 and 12.0 < errs[1] / errs[2] < 20.0
