@@ -402,6 +402,30 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
 
         out["batched"]["cpu_baseline"] = _oracle_sample(
             run, UNIT, "FP64 oracle Algorithm 1 (2 updates) on the 8 smallest problems of the batch")
+    # flow: the N = 4096 Fourier-curve shoot (mixed, 100 steps) carrying a 128 x 128 grid (Eq. u)
+    fc = workloads.fourier_curve_warp()
+    Xf = torch.tensor(fc.X, device=dev)
+    pf = torch.tensor(0.002 * (fc.Y - fc.X), device=dev)
+    gx = np.linspace(0.05, 0.95, 128)
+    grid = torch.tensor(np.stack(np.meshgrid(gx, gx), -1).reshape(-1, 2), device=dev)
+    prmf = ep.params(dim=2, kernel=fc.kernel, sigma=fc.sigma, steps=fc.steps, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    ms, _ = _events_ms(torch, stream, lambda: ep.flow(Xf, pf, grid, prmf), 3)
+    m = grid.shape[0]
+    tpairs = m * fc.n * 4 * fc.steps
+    ppairs = fc.n * fc.n * 4 * fc.steps
+    out["flow"] = {"workload": "fourier_curve_warp N=4096 shoot (Gaussian 0.1, 100 steps, mixed) carrying a 128x128 grid",
+                   "ms_per_flow": ms, "points_per_s": m / (ms * 1e-3),
+                   "target_pairs": tpairs, "particle_pairs": ppairs,
+                   "pair_interactions_per_s": (tpairs + ppairs) / (ms * 1e-3),
+                   "roofline": _alu_roofline((tpairs * 8 + ppairs * FLOPS_PER_PAIR_2D_GAUSS) / (ms * 1e-3), peak_tflops,
+                                             "8 flop per target pair (Eq. u), 19 per particle pair; the particle "
+                                             "shoot is recorded stage by stage")}
+    if with_cpu:
+        gs = grid.cpu().numpy()[::64]
+        out["flow"]["cpu_baseline"] = _oracle_sample(
+            lambda o: (o.flow(fc.X, 0.002 * (fc.Y - fc.X), gs, fc.kernel, fc.sigma, 2),
+                       (gs.shape[0] * fc.n + fc.n * fc.n) * 8)[1],
+            UNIT, f"FP64 oracle flow of {gs.shape[0]} grid points through 2 RK4 steps of the N=4096 shoot")
     # circle -> ellipse, 64 landmarks, tent, FP64 plain method, full Algorithm 1
     c = workloads.circle_to_ellipse()
     Xc, Yc = torch.tensor(c.X, device=dev), torch.tensor(c.Y, device=dev)

@@ -166,6 +166,26 @@ ep_status ep_cell_neighbors(const ep_params* params, int64_t n, const double* q,
 ep_status ep_rhs_noalloc(const ep_params* params, int64_t n, const double* q, const double* p,
                          double* dq, double* dp, void* stream);
 
+/* Velocity field of the particles' momenta at m points (Sec. 3.1, Eq. u):
+ *   u(x_k) = sum_{j=1..n} G(|x_k - q_j|) p_j.
+ * q, p: (n, dim); x, u: (m, dim); row-major FP64, device or host memory (host
+ * arrays are staged and the call then synchronises).  All pairs over the n
+ * particles in params->precision (EP_MIXED: FP32 pair terms, FP32 sums, FP64
+ * result); params->neigh must not be EP_CELLLIST.  x and u may alias.  Errors:
+ * EP_EINVAL for bad sizes, NULL arrays or parameters. */
+ep_status ep_velocity(const ep_params* params, int64_t n, const double* q, const double* p, int64_t m,
+                      const double* x, double* u, void* stream);
+
+/* Transport of m points by the flow of the shoot from (q0, p0): Eq. u integrated
+ * together with Eq. N-particle by the shoot's RK4 (params->steps steps on
+ * [0, params->t1]), so x1 = phi_t1(x0) -- the deformation the momenta define, of
+ * a grid or of any point set.  Arrays and rules as ep_velocity; x1 may alias x0.
+ * The particles' own endpoint is ep_shoot's.  Memory: the particle state of
+ * every RK4 stage is recorded, (4 steps + 1) x n x (16 B mixed 2-D, 32 B mixed
+ * 3-D, 16 dim B FP64). */
+ep_status ep_flow(const ep_params* params, int64_t n, const double* q0, const double* p0, int64_t m,
+                  const double* x0, double* x1, void* stream);
+
 /* Free the cached device workspaces of every stream (synchronises the device). */
 ep_status ep_release_workspace(void);
 

@@ -355,6 +355,18 @@ const char* ep_last_error(void) { return g_err; }
 
 ep_status ep_release_workspace(void) { return release_all_arenas(); }
 
+ep_status ep_velocity(const ep_params* params, int64_t n, const double* q, const double* p, int64_t m,
+                      const double* x, double* u, void* stream)
+{
+    return velocity_entry(params, n, q, p, m, x, u, stream);
+}
+
+ep_status ep_flow(const ep_params* params, int64_t n, const double* q0, const double* p0, int64_t m,
+                  const double* x0, double* x1, void* stream)
+{
+    return flow_entry(params, n, q0, p0, m, x0, x1, stream);
+}
+
 ep_status ep_rhs(const ep_params* params, int64_t n, const double* q, const double* p, double* dq,
                  double* dp, void* stream)
 {

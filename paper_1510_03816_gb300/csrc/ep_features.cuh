@@ -31,6 +31,10 @@ ep_status adjoint_entry(const ep_params* params, int64_t n, const double* X, con
                         void* stream);
 ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offsets, const double* X,
                         const double* Y, double* p0, ep_match_info* infos, void* stream);
+ep_status velocity_entry(const ep_params* params, int64_t n, const double* q, const double* p, int64_t m,
+                         const double* x, double* u, void* stream);
+ep_status flow_entry(const ep_params* params, int64_t n, const double* q0, const double* p0, int64_t m,
+                     const double* x0, double* x1, void* stream);
 // ep_match of one small 2-D mixed-precision problem, solved entirely on one CTA.
 ep_status match_small(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
                       ep_match_info* info, void* stream);

@@ -34,7 +34,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libep.so")
 EXPORTS = ("ep_rhs", "ep_shoot", "ep_match", "ep_adjoint", "ep_match_batched", "ep_hamiltonian",
            "ep_hvp", "ep_cell_neighbors", "ep_release_workspace", "ep_last_error", "ep_version",
            "ep_launch_count", "ep_rhs_noalloc", "ep_set_launch_timing", "ep_last_launch_ms",
-           "ep_last_launch_kernel")
+           "ep_last_launch_kernel", "ep_velocity", "ep_flow")
 
 
 class EPError(RuntimeError):
@@ -91,6 +91,8 @@ def load():
         "ep_hvp": [P, I64, VP, VP, VP, VP, VP, VP, VP],
         "ep_cell_neighbors": [P, I64, VP, VP, VP, VP, VP],
         "ep_release_workspace": [],
+        "ep_velocity": [P, I64, VP, VP, I64, VP, VP, VP],
+        "ep_flow": [P, I64, VP, VP, I64, VP, VP, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -230,6 +232,34 @@ def shoot(q0, p0, prm: Params):
     q1, p1 = _empty_like(q0), _empty_like(q0)
     _check(load().ep_shoot(ctypes.byref(_with_dim(prm, dim)), n, qp, pp, _ptr(q1), _ptr(p1), _stream_for(q0)))
     return q1, p1
+
+
+def velocity(q, p, x, prm: Params):
+    """ep_velocity: u(x_k) = sum_j G(|x_k - q_j|) p_j at the points x (Eq. u)."""
+    q, qp = _prep(q, "q")
+    p, pp = _prep(p, "p")
+    x, xp = _prep(x, "x")
+    n, dim = _shape(q)
+    m, xdim = _shape(x)
+    if xdim != dim:
+        raise ValueError(f"x has dimension {xdim}, the particles {dim}")
+    u = _empty_like(x)
+    _check(load().ep_velocity(ctypes.byref(_with_dim(prm, dim)), n, qp, pp, m, xp, _ptr(u), _stream_for(x)))
+    return u
+
+
+def flow(q0, p0, x0, prm: Params):
+    """ep_flow: the points x0 carried by the flow of the shoot from (q0, p0) -> x1."""
+    q0, qp = _prep(q0, "q0")
+    p0, pp = _prep(p0, "p0")
+    x0, xp = _prep(x0, "x0")
+    n, dim = _shape(q0)
+    m, xdim = _shape(x0)
+    if xdim != dim:
+        raise ValueError(f"x0 has dimension {xdim}, the particles {dim}")
+    x1 = _empty_like(x0)
+    _check(load().ep_flow(ctypes.byref(_with_dim(prm, dim)), n, qp, pp, m, xp, _ptr(x1), _stream_for(x0)))
+    return x1
 
 
 def hamiltonian(q, p, prm: Params) -> float:

@@ -46,8 +46,9 @@ MUTANTS = {
                                   "orc_velocity(dim, kernel, sigma, n, q1, p1, m, yx, k4x);"),
 }
 # mutations applied at every occurrence: these lines appear both in the full
-# function and in its row-sampled variant (orc_rhs_rows, orc_cell_neighbors_rows)
-EVERYWHERE = {"cell_predicate_le", "rhs_dq_drops_self_term", "rhs_dp_sign", "rhs_dp_uses_pi_twice"}
+# function and in its row-sampled variant (orc_rhs_rows, orc_cell_neighbors_rows),
+# or in both RK4 integrators (the shoot and the flow)
+EVERYWHERE = {"cell_predicate_le", "rhs_dq_drops_self_term", "rhs_dp_sign", "rhs_dp_uses_pi_twice", "rk4_weight"}
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
