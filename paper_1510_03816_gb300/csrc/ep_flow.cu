@@ -10,8 +10,9 @@
 //   x_{n+1} = x_n + dt/6 (k1 + 2 k2 + 2 k3 + k4),
 // which is the joint RK4 of (q, p, x) because x never feeds back into (q, p).
 // Targets are independent, so one launch covers the whole flow with no grid
-// synchronisation: a CTA owns 512 targets (2 per thread) and, stage by stage,
-// streams the recorded particle copy through shared memory.
+// synchronisation: a CTA owns 64 targets and, stage by stage, streams the
+// recorded particle copy through shared memory, its 8 warps splitting the
+// particles.
 //
 // Mixed precision: the particle copies are the FP32 scaled records of the
 // all-pairs path (q' = s (q - c0)); a target's stage position is formed in FP64
@@ -30,7 +31,8 @@ namespace ep {
 namespace {
 
 constexpr int kFlowThreads = 256;
-constexpr int kFlowRT = 2;         // targets per thread
+constexpr int kFlowRT = 2;         // targets per lane
+constexpr int kFlowTile = 32 * kFlowRT;  // targets per CTA
 constexpr int kFlowChunk = 2048;   // particle records per shared-memory fill (mixed)
 constexpr int kFlowChunk64 = 1024; // (FP64)
 
@@ -91,48 +93,56 @@ struct Rk4 {
     }
 };
 
+// One CTA: kFlowTile targets (lane l of every warp holds targets l and l + 32);
+// the 8 warps split each staged chunk of particles, their partial velocities are
+// summed in shared memory, and warp 0 applies the RK4 stage and publishes the
+// targets' next stage positions.
 template <int DIM, int KER>
 __global__ void __launch_bounds__(kFlowThreads) k_flow_mixed(FlowArgs a)
 {
     constexpr int V = DIM == 2 ? 1 : 2;
-    extern __shared__ float4 sm[];
-    const int n = a.n;
+    constexpr int W = kFlowThreads / 32;
+    extern __shared__ float4 sm[];                                  // [V * kFlowChunk]
+    __shared__ float s_y[kFlowTile][DIM];                           // targets' stage positions (scaled)
+    __shared__ float s_red[W][kFlowTile][DIM];                      // warps' partial velocities
+    const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double c0[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) c0[c] = a.c0[c];
     int tgt[kFlowRT];
-    Rk4 st[kFlowRT][DIM];
+    Rk4 st[kFlowRT][DIM];  // meaningful in warp 0
 #pragma unroll
     for (int r = 0; r < kFlowRT; ++r) {
-        tgt[r] = blockIdx.x * (kFlowThreads * kFlowRT) + threadIdx.x + kFlowThreads * r;
+        tgt[r] = blockIdx.x * kFlowTile + lane + 32 * r;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
             const double v = tgt[r] < a.m ? a.x0[(size_t)tgt[r] * DIM + c] : 0.0;
             st[r][c].x = v;
             st[r][c].y = v;
             st[r][c].acc = 0.0;
+            if (warp == 0) s_y[lane + 32 * r][c] = (float)((v - c0[c]) * a.s);
         }
     }
     const int nst = a.steps == 0 ? 1 : 4 * a.steps;
     for (int k = 0; k < nst; ++k) {
         const float4* copy = a.rec + (size_t)k * V * n;
-        float y[kFlowRT][DIM];
+        __syncthreads();
+        float y[kFlowRT][DIM], u[kFlowRT][DIM];
 #pragma unroll
         for (int r = 0; r < kFlowRT; ++r)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) y[r][c] = (float)((st[r][c].y - c0[c]) * a.s);
-        float u[kFlowRT][DIM];
-#pragma unroll
-        for (int r = 0; r < kFlowRT; ++r)
-#pragma unroll
-            for (int c = 0; c < DIM; ++c) u[r][c] = 0.0f;
+            for (int c = 0; c < DIM; ++c) {
+                y[r][c] = s_y[lane + 32 * r][c];
+                u[r][c] = 0.0f;
+            }
         for (int cj = 0; cj < n; cj += kFlowChunk) {
             const int L = min(kFlowChunk, n - cj);
-            __syncthreads();
+            if (cj > 0) __syncthreads();
             for (int t = threadIdx.x; t < L * V; t += kFlowThreads) sm[t] = __ldg(copy + (size_t)cj * V + t);
             __syncthreads();
+            const int ja = warp * L / W, jb = (warp + 1) * L / W;
 #pragma unroll 2
-            for (int j = 0; j < L; ++j) {
+            for (int j = ja; j < jb; ++j) {
                 float qj[DIM], pj[DIM];
                 if constexpr (DIM == 2) {
                     const float4 v = sm[j];
@@ -160,60 +170,82 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_mixed(FlowArgs a)
 #pragma unroll
         for (int r = 0; r < kFlowRT; ++r)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) {
-                if (a.steps == 0)
-                    st[r][c].x = (double)u[r][c];
-                else
-                    st[r][c].stage(k & 3, (double)u[r][c], a.dt);
-            }
+            for (int c = 0; c < DIM; ++c) s_red[warp][lane + 32 * r][c] = u[r][c];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int r = 0; r < kFlowRT; ++r)
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) {
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int w2 = 0; w2 < W; ++w2) sum += s_red[w2][lane + 32 * r][c];
+                    if (a.steps == 0) {
+                        st[r][c].x = (double)sum;
+                    } else {
+                        st[r][c].stage(k & 3, (double)sum, a.dt);
+                        s_y[lane + 32 * r][c] = (float)((st[r][c].y - c0[c]) * a.s);
+                    }
+                }
+        }
     }
+    if (warp == 0)
 #pragma unroll
-    for (int r = 0; r < kFlowRT; ++r)
-        if (tgt[r] < a.m)
+        for (int r = 0; r < kFlowRT; ++r)
+            if (tgt[r] < a.m)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) a.x1[(size_t)tgt[r] * DIM + c] = st[r][c].x;
+                for (int c = 0; c < DIM; ++c) a.x1[(size_t)tgt[r] * DIM + c] = st[r][c].x;
 }
 
 template <int DIM, int KER>
 __global__ void __launch_bounds__(kFlowThreads) k_flow_fp64(FlowArgs a)
 {
     constexpr int S2 = 2 * DIM;
-    extern __shared__ double dsm[];
-    const int n = a.n;
+    constexpr int W = kFlowThreads / 32;
+    extern __shared__ double dsm[];                                 // [S2 * kFlowChunk64]
+    __shared__ double s_y[kFlowTile][DIM];
+    __shared__ double s_red[W][kFlowTile][DIM];
+    const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int tgt[kFlowRT];
-    Rk4 st[kFlowRT][DIM];
+    Rk4 st[kFlowRT][DIM];  // meaningful in warp 0
 #pragma unroll
     for (int r = 0; r < kFlowRT; ++r) {
-        tgt[r] = blockIdx.x * (kFlowThreads * kFlowRT) + threadIdx.x + kFlowThreads * r;
+        tgt[r] = blockIdx.x * kFlowTile + lane + 32 * r;
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
             const double v = tgt[r] < a.m ? a.x0[(size_t)tgt[r] * DIM + c] : 0.0;
             st[r][c].x = v;
             st[r][c].y = v;
             st[r][c].acc = 0.0;
+            if (warp == 0) s_y[lane + 32 * r][c] = v;
         }
     }
     const int nst = a.steps == 0 ? 1 : 4 * a.steps;
     for (int k = 0; k < nst; ++k) {
         const double* copy = a.drec + (size_t)k * S2 * n;
-        double u[kFlowRT][DIM];
+        __syncthreads();
+        double y[kFlowRT][DIM], u[kFlowRT][DIM];
 #pragma unroll
         for (int r = 0; r < kFlowRT; ++r)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) u[r][c] = 0.0;
+            for (int c = 0; c < DIM; ++c) {
+                y[r][c] = s_y[lane + 32 * r][c];
+                u[r][c] = 0.0;
+            }
         for (int cj = 0; cj < n; cj += kFlowChunk64) {
             const int L = min(kFlowChunk64, n - cj);
-            __syncthreads();
+            if (cj > 0) __syncthreads();
             for (int t = threadIdx.x; t < L * S2; t += kFlowThreads) dsm[t] = __ldg(copy + (size_t)cj * S2 + t);
             __syncthreads();
-            for (int j = 0; j < L; ++j) {
+            const int ja = warp * L / W, jb = (warp + 1) * L / W;
+            for (int j = ja; j < jb; ++j) {
                 const double* v = dsm + (size_t)j * S2;
 #pragma unroll
                 for (int r = 0; r < kFlowRT; ++r) {
                     double r2 = 0.0;
 #pragma unroll
                     for (int c = 0; c < DIM; ++c) {
-                        const double d = st[r][c].y - v[c];
+                        const double d = y[r][c] - v[c];
                         r2 += d * d;
                     }
                     double G, phi;
@@ -226,24 +258,37 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_fp64(FlowArgs a)
 #pragma unroll
         for (int r = 0; r < kFlowRT; ++r)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) {
-                if (a.steps == 0)
-                    st[r][c].x = u[r][c];
-                else
-                    st[r][c].stage(k & 3, u[r][c], a.dt);
-            }
+            for (int c = 0; c < DIM; ++c) s_red[warp][lane + 32 * r][c] = u[r][c];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int r = 0; r < kFlowRT; ++r)
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w2 = 0; w2 < W; ++w2) sum += s_red[w2][lane + 32 * r][c];
+                    if (a.steps == 0) {
+                        st[r][c].x = sum;
+                    } else {
+                        st[r][c].stage(k & 3, sum, a.dt);
+                        s_y[lane + 32 * r][c] = st[r][c].y;
+                    }
+                }
+        }
     }
+    if (warp == 0)
 #pragma unroll
-    for (int r = 0; r < kFlowRT; ++r)
-        if (tgt[r] < a.m)
+        for (int r = 0; r < kFlowRT; ++r)
+            if (tgt[r] < a.m)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) a.x1[(size_t)tgt[r] * DIM + c] = st[r][c].x;
+                for (int c = 0; c < DIM; ++c) a.x1[(size_t)tgt[r] * DIM + c] = st[r][c].x;
 }
 
 template <int DIM, int KER>
 ep_status launch_flow(const ep_params& P, FlowArgs& a, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)((a.m + kFlowThreads * kFlowRT - 1) / (kFlowThreads * kFlowRT));
+    const unsigned grid = (unsigned)((a.m + kFlowTile - 1) / kFlowTile);
     if (grid == 0) return EP_OK;
     count_launch();
     if (P.precision == EP_MIXED) {
