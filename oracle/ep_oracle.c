@@ -23,7 +23,9 @@
  *     definition of the GPU path's FP32 acceptance test; see orc_cell_*)
  *   - the velocity field at arbitrary points             (Sec. 3.1, Eq. u)
  *     and the transport of points by the flow it generates along a shoot
- *     (the deformation phi_t with d phi_t(x)/dt = u(phi_t(x), t)).
+ *     (the deformation phi_t with d phi_t(x)/dt = u(phi_t(x), t))
+ *   - the inexact particle system, its shoot and its matching loop with the
+ *     momentum-difference stop                           (Sec. 6, Eq. N-particle-inexact).
  *
  * Parity pins (tests/test_oracle_pins.py): every function here is checked
  * against something other than itself -- finite differences of H, closed
@@ -349,6 +351,108 @@ int orc_match(int dim, int kernel, double sigma, int steps, double t1, long n, c
         if (k == maxit) { status = ORC_ENOTCONVERGED; break; }
         for (long a = 0; a < m; ++a) p0[a] += h * (Y[a] - q1[a]);
         ++k;
+    }
+    if (iters) *iters = k;
+    if (resid) *resid = res;
+    free(q1);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. N-particle-inexact (Sec. 6): the inexact-matching particle system.    */
+/*   dq_i/dt = sum_j G(|q_i - q_j|) p_j + s2 p_i      (s2 = sigma_n^2 > 0)     */
+/*   dp_i/dt = as in Eq. N-particle.                                         */
+/* ------------------------------------------------------------------------ */
+void orc_rhs_inexact(int dim, int kernel, double sigma, double s2, long n, const double* q, const double* p,
+                     double* dq, double* dp)
+{
+    orc_rhs(dim, kernel, sigma, n, q, p, dq, dp);
+    for (long a = 0; a < n * dim; ++a) dq[a] += s2 * p[a];
+}
+
+/* Classical RK4 of the inexact system (the shoot's scheme). */
+int orc_shoot_inexact(int dim, int kernel, double sigma, double s2, int steps, double t1, long n,
+                      const double* q0, const double* p0, double* q1, double* p1)
+{
+    if (dim < 1 || dim > 3 || steps < 1 || n < 0) return ORC_EINVAL;
+    long a, m = n * dim;
+    double* w = (double*)malloc(sizeof(double) * (size_t)(10 * m + 1));
+    if (!w) return ORC_EINVAL;
+    double *k1q = w, *k1p = w + m, *k2q = w + 2 * m, *k2p = w + 3 * m, *k3q = w + 4 * m;
+    double *k3p = w + 5 * m, *k4q = w + 6 * m, *k4p = w + 7 * m, *yq = w + 8 * m, *yp = w + 9 * m;
+    memcpy(q1, q0, sizeof(double) * (size_t)m);
+    memcpy(p1, p0, sizeof(double) * (size_t)m);
+    double dt = t1 / steps;
+    for (int s = 0; s < steps; ++s) {
+        orc_rhs_inexact(dim, kernel, sigma, s2, n, q1, p1, k1q, k1p);
+        for (a = 0; a < m; ++a) { yq[a] = q1[a] + 0.5 * dt * k1q[a]; yp[a] = p1[a] + 0.5 * dt * k1p[a]; }
+        orc_rhs_inexact(dim, kernel, sigma, s2, n, yq, yp, k2q, k2p);
+        for (a = 0; a < m; ++a) { yq[a] = q1[a] + 0.5 * dt * k2q[a]; yp[a] = p1[a] + 0.5 * dt * k2p[a]; }
+        orc_rhs_inexact(dim, kernel, sigma, s2, n, yq, yp, k3q, k3p);
+        for (a = 0; a < m; ++a) { yq[a] = q1[a] + dt * k3q[a]; yp[a] = p1[a] + dt * k3p[a]; }
+        orc_rhs_inexact(dim, kernel, sigma, s2, n, yq, yp, k4q, k4p);
+        for (a = 0; a < m; ++a) {
+            q1[a] += dt / 6.0 * (k1q[a] + 2.0 * k2q[a] + 2.0 * k3q[a] + k4q[a]);
+            p1[a] += dt / 6.0 * (k1p[a] + 2.0 * k2p[a] + 2.0 * k3p[a] + k4p[a]);
+        }
+    }
+    free(w);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 on the inexact system with the stopping rule of Sec. 6: stop  */
+/* when the initial momenta of two consecutive iterates differ by less than  */
+/* eps (maximum norm).  Each iterate shoots, records the residual            */
+/* |Y - Q(1)|_inf, and updates p0 <- p0 + h (Y - Q(1)); the loop ends after  */
+/* the update whose size is below eps (converged), at maxit updates (not     */
+/* converged) or at a non-finite residual (diverged).  h <= 0 selects        */
+/* 1 / (max_i sum_j |G_ij| + s2), the Gershgorin bound on lambda_max of the  */
+/* linearised map G(X) + s2 I.  *iters counts updates; *resid is the last    */
+/* shoot's residual.                                                         */
+/* ------------------------------------------------------------------------ */
+int orc_match_inexact(int dim, int kernel, double sigma, double s2, int steps, double t1, long n,
+                      const double* X, const double* Y, double h, double eps, int maxit, double* p0,
+                      int* iters, double* resid, double* hist)
+{
+    if (dim < 1 || dim > 3 || steps < 1 || n < 0 || maxit < 0) return ORC_EINVAL;
+    long m = n * dim;
+    double* q1 = (double*)malloc(sizeof(double) * (size_t)(2 * m + 1));
+    double* p1 = q1 + m;
+    if (!q1) return ORC_EINVAL;
+    if (h <= 0.0) {
+        double best = 0.0;
+        for (long i = 0; i < n; ++i) {
+            double row = 0.0;
+            for (long j = 0; j < n; ++j) row += fabs(orc_G(kernel, sigma, dist(dim, X + i * dim, X + j * dim)));
+            if (row > best) best = row;
+        }
+        h = 1.0 / (best + s2);
+    }
+    int status = ORC_ENOTCONVERGED;
+    int k = 0;
+    double res = 0.0;
+    for (;;) {
+        orc_shoot_inexact(dim, kernel, sigma, s2, steps, t1, n, X, p0, q1, p1);
+        res = 0.0;
+        int finite = 1;
+        for (long a = 0; a < m; ++a) {
+            double r = Y[a] - q1[a];
+            if (!isfinite(r)) finite = 0;
+            if (fabs(r) > res) res = fabs(r);
+        }
+        if (!finite) res = NAN;
+        if (hist) hist[k] = res;
+        if (!finite) { status = ORC_EDIVERGED; break; }
+        if (k == maxit) { status = ORC_ENOTCONVERGED; break; }
+        double dmax = 0.0;
+        for (long a = 0; a < m; ++a) {
+            double d = h * (Y[a] - q1[a]);
+            p0[a] += d;
+            if (fabs(d) > dmax) dmax = fabs(d);
+        }
+        ++k;
+        if (dmax < eps) { status = ORC_OK; break; }
     }
     if (iters) *iters = k;
     if (resid) *resid = res;

@@ -90,6 +90,12 @@ def _load():
         lib.orc_velocity.argtypes = [i, i, d, l, p, p, l, p, p]
         lib.orc_flow.restype = i
         lib.orc_flow.argtypes = [i, i, d, i, d, l, p, p, l, p, p, p, p]
+        lib.orc_rhs_inexact.restype = None
+        lib.orc_rhs_inexact.argtypes = [i, i, d, d, l, p, p, p, p]
+        lib.orc_shoot_inexact.restype = i
+        lib.orc_shoot_inexact.argtypes = [i, i, d, d, i, d, l, p, p, p, p]
+        lib.orc_match_inexact.restype = i
+        lib.orc_match_inexact.argtypes = [i, i, d, d, i, d, l, p, p, d, d, i, p, p, p, p]
         lib.orc_set_threads.restype = None
         lib.orc_set_threads.argtypes = [i]
         lib.orc_max_threads.restype = i
@@ -293,3 +299,42 @@ def flow(q0, p0, x0, kernel: int, sigma: float, steps: int, t1: float = 1.0):
     if st != 0:
         raise ValueError("orc_flow: invalid arguments")
     return q1, p1, x1
+
+
+def rhs_inexact(q, p, kernel: int, sigma: float, s2: float):
+    """Eq. N-particle-inexact: dq gains s2 p_i (s2 = sigma_n^2)."""
+    q = _arr(q)
+    dim = q.shape[1]
+    p = _arr(p, dim)
+    dq, dp = np.empty_like(q), np.empty_like(q)
+    _load().orc_rhs_inexact(dim, kernel, sigma, s2, q.shape[0], _ptr(q), _ptr(p), _ptr(dq), _ptr(dp))
+    return dq, dp
+
+
+def shoot_inexact(q0, p0, kernel: int, sigma: float, s2: float, steps: int, t1: float = 1.0):
+    q0 = _arr(q0)
+    dim = q0.shape[1]
+    p0 = _arr(p0, dim)
+    q1, p1 = np.empty_like(q0), np.empty_like(p0)
+    if _load().orc_shoot_inexact(dim, kernel, sigma, s2, steps, t1, q0.shape[0], _ptr(q0), _ptr(p0), _ptr(q1),
+                                 _ptr(p1)) != 0:
+        raise ValueError("orc_shoot_inexact: invalid arguments")
+    return q1, p1
+
+
+def match_inexact(X, Y, kernel: int, sigma: float, s2: float, steps: int, h: float = 0.0, eps: float = 1e-6,
+                  maxit: int = 200, p0=None, t1: float = 1.0):
+    """Algorithm 1 on the inexact system with the momentum-difference stop:
+    returns (p0, status, iters, resid, hist)."""
+    X = _arr(X)
+    dim = X.shape[1]
+    Y = _arr(Y, dim)
+    p = np.zeros_like(X) if p0 is None else _arr(p0, dim).copy()
+    it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+    hist = np.full(maxit + 1, np.nan)
+    st = _load().orc_match_inexact(dim, kernel, sigma, s2, steps, t1, X.shape[0], _ptr(X), _ptr(Y), h, eps, maxit,
+                                   _ptr(p), ctypes.byref(it), ctypes.byref(res), _ptr(hist))
+    if st == EINVAL:
+        raise ValueError("orc_match_inexact: invalid arguments")
+    shoots = it.value if st == OK else it.value + 1  # a converged loop ends on an update
+    return p, st, it.value, res.value, hist[:shoots]

@@ -42,6 +42,10 @@ MUTANTS = {
                           "for (a = 0; a < md; ++a) yx[a] = x1[a] + 0.5 * dt * k1x[a];"),
     "flow_weights": ("x1[a] += dt / 6.0 * (k1x[a] + 2.0 * k2x[a] + 2.0 * k3x[a] + k4x[a]);",
                      "x1[a] += dt / 6.0 * (k1x[a] + 2.0 * k2x[a] + 1.0 * k3x[a] + 2.0 * k4x[a]);"),
+    "inexact_term_sign": ("for (long a = 0; a < n * dim; ++a) dq[a] += s2 * p[a];",
+                          "for (long a = 0; a < n * dim; ++a) dq[a] -= s2 * p[a];"),
+    "inexact_stop_on_residual": ("if (fabs(d) > dmax) dmax = fabs(d);",
+                                 "if (fabs(d) / h > dmax) dmax = fabs(d) / h;"),
     "flow_stale_velocity_stage": ("orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k4x);",
                                   "orc_velocity(dim, kernel, sigma, n, q1, p1, m, yx, k4x);"),
 }

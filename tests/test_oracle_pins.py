@@ -449,3 +449,66 @@ def test_flow_of_one_particle_matches_an_ode_solver_and_is_fourth_order():
         errs.append(np.abs(x1 - ref).max())
     assert errs[2] < 1e-8
     assert 12.0 < errs[0] / errs[1] < 20.0 and 12.0 < errs[1] / errs[2] < 20.0
+
+
+# --------------------------------------------------------------------------- the inexact system (Sec. 6)
+
+
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_inexact_rhs_is_the_symplectic_gradient_of_the_augmented_H(kernel, sigma, dim):
+    """Eq. N-particle-inexact is Hamiltonian with H + (s2 / 2) sum_i |p_i|^2: dq = dH/dp,
+    dp = -dH/dq, checked by central differences of the plain double sum of Eq. H."""
+    s2 = 0.37
+    q, p = _cloud(7, dim, seed=50 + dim + kernel, spread=0.8, pscale=0.3, min_gap=0.05, sigma=sigma, kernel=kernel)
+    dq, dp = o.rhs_inexact(q, p, kernel, sigma, s2)
+
+    def Ha(qq, pp):
+        return o.hamiltonian(qq, pp, kernel, sigma) + 0.5 * s2 * np.sum(pp * pp)
+
+    eps = 1e-6
+    for i in range(q.shape[0]):
+        for c in range(dim):
+            e = np.zeros_like(q)
+            e[i, c] = eps
+            fdp = (Ha(q, p + e) - Ha(q, p - e)) / (2 * eps)
+            fdq = (Ha(q + e, p) - Ha(q - e, p)) / (2 * eps)
+            assert abs(fdp - dq[i, c]) < 1e-8 * max(1.0, abs(dq[i, c]))
+            assert abs(-fdq - dp[i, c]) < 1e-7 * max(1.0, abs(dp[i, c]))
+
+
+def test_inexact_shoot_reduces_to_the_exact_one_and_moves_one_particle_straight():
+    q, p = _cloud(9, 2, seed=52, spread=0.7, pscale=0.2, min_gap=0.02)
+    qa, pa = o.shoot_inexact(q, p, o.GAUSS, 0.3, 0.0, 11)
+    qb, pb = o.shoot(q, p, o.GAUSS, 0.3, 11)
+    np.testing.assert_array_equal(qa, qb)
+    np.testing.assert_array_equal(pa, pb)
+    # one particle: p constant, q(t) = q0 + (G(0) + s2) p0 t
+    X, p0 = np.array([[0.2, 0.3]]), np.array([[0.05, -0.02]])
+    q1, p1 = o.shoot_inexact(X, p0, o.TENT, 0.2, 0.3, 7)
+    np.testing.assert_allclose(q1, X + 1.3 * p0, rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(p1, p0)
+
+
+def test_inexact_match_stops_on_the_momentum_difference():
+    """One particle: Q(1) = X + (1 + s2) p, so p_k = c (1 - (1 - h (1 + s2))^k) with
+    c = (Y - X) / (1 + s2), and the update at iterate k is h (1 + s2) (c - p_k); the loop
+    stops after the first update smaller than eps."""
+    s2, h, eps = 0.5, 0.3, 1e-6
+    X, Y = np.array([[0.2, 0.3]]), np.array([[0.26, 0.27]])
+    c = (Y - X) / (1 + s2)
+    a = 1 - h * (1 + s2)
+    k = 0
+    while True:
+        upd = np.abs(h * (1 + s2) * c * a ** k).max()
+        k += 1
+        if upd < eps:
+            break
+    p, st, it, res, hist = o.match_inexact(X, Y, o.GAUSS, 0.1, s2, 3, h=h, eps=eps, maxit=500)
+    assert st == o.OK and it == k
+    np.testing.assert_allclose(p, c * (1 - a ** k), rtol=0, atol=1e-15)
+    assert len(hist) == k and abs(hist[0] - np.abs(Y - X).max()) < 1e-15
+    # the default gain is 1 / (max row sum + s2)
+    p, st, it, res, hist = o.match_inexact(X, Y, o.GAUSS, 0.1, s2, 3, eps=eps, maxit=500)
+    np.testing.assert_allclose(p, c, rtol=0, atol=1e-15)  # h = 1 / (1 + s2): exact after one update
+    assert st == o.OK and it == 2
