@@ -439,6 +439,17 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
                                 "shoots_per_s": (r.iters + 1) / dt,
                                 "roofline": {"bound": "latency", "note": "one CTA, 200 dependent shoots of 200 "
                                              "dependent RHS; reported as shoots/s"}}
+    # the inexact system (Sec. 6): circle -> ellipse, sigma_n^2 = 0.05, FP64, momentum-difference stop
+    prmi = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.FP64, neigh=ep.ALLPAIRS,
+                     inexact=0.05)
+    t0 = time.perf_counter()
+    r = ep.match(Xc, Yc, prmi, h=0.0, eps=c.eps, maxit=c.maxit)
+    dt = time.perf_counter() - t0
+    out["inexact_fp64"] = {"workload": "circle_to_ellipse N=64, tent sigma=0.25, sigma_n^2=0.05, 50 steps, FP64, "
+                                       "stop on |p0^(k+1) - p0^(k)| < 1e-6",
+                           "seconds_per_match": dt, "iters": r.iters, "status": r.status, "resid": r.resid,
+                           "shoots_per_s": r.iters / dt,
+                           "roofline": {"bound": "latency", "note": "one cooperative launch, FP64 pairs on 64 SMs"}}
     if with_cpu:
         def run_small(o):
             _, _, it, _, _ = o.match(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.0, eps=c.eps, maxit=c.maxit)

@@ -62,13 +62,22 @@ typedef struct {
     double t1;      /* end time; 1.0 for the matching problem (Eq. exact-matching) */
     int precision;  /* ep_precision */
     int neigh;      /* ep_neigh */
+    double inexact; /* sigma_n^2 >= 0 of the inexact particle system (Sec. 6, Eq.
+                       N-particle-inexact): dq_i gains inexact * p_i.  0 = the exact
+                       system.  With inexact > 0, ep_match stops when two consecutive
+                       initial momenta differ by less than eps (Sec. 6) and its default
+                       gain is 1 / (max_i sum_j G_ij + inexact).  Supported on the
+                       all-pairs paths of ep_rhs, ep_shoot, ep_match and ep_rhs_noalloc;
+                       the cell list, ep_match_batched, ep_hvp, ep_adjoint, ep_velocity
+                       and ep_flow return EP_EINVAL for inexact != 0. */
 } ep_params;
 
 typedef struct {
     double h;        /* in: gain of M = h I (<= 0: h = 1 / max_i sum_j G_ij); out: gain used */
     double eps;      /* in: stop when max_i,c |Y - Q(1)| < eps */
     int maxit;       /* in: maximum number of momentum updates (>= 0) */
-    int iters;       /* out: number of updates performed (shoots = iters + 1) */
+    int iters;       /* out: number of updates performed (shoots = iters + 1; iters when an
+                        inexact matching converges, since it ends on an update) */
     double resid_inf;/* out: max-norm residual of the last shoot */
     double H;        /* out: Hamiltonian H(X, p0) of Eq. H for the returned p0 */
     double* hist;    /* in, optional: maxit + 1 doubles (host or device) that receive the

@@ -615,6 +615,7 @@ ep_status hvp_entry(const ep_params* params, int64_t n, const double* q, const d
                     const double* vp, double* hq, double* hp, void* stream)
 {
     EP_TRY(check_params(params));
+    if (params->inexact != 0.0) return set_error("the Hessian and the adjoint are built for the exact system"), EP_EINVAL;
     if (n < 0 || n > ((int64_t)1 << 26)) return set_error("ep_hvp: bad n"), EP_EINVAL;
     if (n == 0) return EP_OK;
     if (!q || !p || !vq || !vp || !hq || !hp) return set_error("ep_hvp: NULL array"), EP_EINVAL;
@@ -665,6 +666,7 @@ ep_status adjoint_entry(const ep_params* params, int64_t n, const double* X, con
                         void* stream)
 {
     EP_TRY(check_params(params));
+    if (params->inexact != 0.0) return set_error("the Hessian and the adjoint are built for the exact system"), EP_EINVAL;
     if (n < 0 || n > ((int64_t)1 << 26)) return set_error("ep_adjoint: bad n"), EP_EINVAL;
     if (ckpt_every < 1) return set_error("ep_adjoint: ckpt_every must be >= 1"), EP_EINVAL;
     if (!isfinite(lambda)) return set_error("ep_adjoint: lambda must be finite"), EP_EINVAL;

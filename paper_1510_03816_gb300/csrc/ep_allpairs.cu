@@ -220,7 +220,8 @@ __device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int co
 {
     float kv;
     if (comp < 2) {
-        kv = comp == 0 ? f[0] : f[1];
+        // dq (+ sigma_n^2 p_i for the inexact system, Sec. 6)
+        kv = fmaf(a.s2_f, comp == 0 ? e.pin.x : e.pin.y, comp == 0 ? f[0] : f[1]);
     } else {
         const float m0 = comp == 2 ? f[2] : f[4], m1 = comp == 2 ? f[3] : f[5];
         kv = a.dp_scale_f * fmaf(m0, e.pin.x, m1 * e.pin.y);
@@ -659,7 +660,8 @@ __device__ void epilogue_fp64(const StageArgs& a, int i, double sigma_unused)
     double kq[DIM], kp[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-        kq[c] = __ldcg(a.K + (size_t)i * kKWidth + c);
+        // dq (+ sigma_n^2 p_i for the inexact system, Sec. 6)
+        kq[c] = __ldcg(a.K + (size_t)i * kKWidth + c) + a.s2 * __ldcg(a.D_in + (size_t)i * 2 * DIM + DIM + c);
         kp[c] = __ldcg(a.K + (size_t)i * kKWidth + 3 + c);
         a.K[(size_t)i * kKWidth + c] = 0.0;
         a.K[(size_t)i * kKWidth + 3 + c] = 0.0;

@@ -20,6 +20,8 @@ struct StageArgs {
     double s;
     double dp_scale;
     float dp_scale_f;
+    double s2;          // sigma_n^2 of the inexact system (Sec. 6), 0 for the exact one
+    float s2_f;
     const double* c0;
     const float4* S_in;
     float4* S_out;
@@ -128,14 +130,14 @@ __device__ void epilogue_mixed_k(const StageArgs& a, int i, const double* kk)
     if (a.mode == MODE_RHS) {
         double kq[DIM], kp[DIM];
         if constexpr (DIM == 2) {
-            kq[0] = kk[0];
-            kq[1] = kk[1];
+            kq[0] = kk[0] + a.s2 * (double)pin[0];
+            kq[1] = kk[1] + a.s2 * (double)pin[1];
             kp[0] = a.dp_scale * (kk[2] * (double)pin[0] + kk[3] * (double)pin[1]);
             kp[1] = a.dp_scale * (kk[4] * (double)pin[0] + kk[5] * (double)pin[1]);
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                kq[c] = kk[c];
+                kq[c] = kk[c] + a.s2 * (double)pin[c];
                 kp[c] = a.dp_scale * kk[3 + c];
             }
         }
@@ -148,14 +150,14 @@ __device__ void epilogue_mixed_k(const StageArgs& a, int i, const double* kk)
     }
     float kq[DIM], kp[DIM];
     if constexpr (DIM == 2) {
-        kq[0] = (float)kk[0];
-        kq[1] = (float)kk[1];
+        kq[0] = fmaf(a.s2_f, pin[0], (float)kk[0]);
+        kq[1] = fmaf(a.s2_f, pin[1], (float)kk[1]);
         kp[0] = a.dp_scale_f * fmaf((float)kk[2], pin[0], (float)kk[3] * pin[1]);
         kp[1] = a.dp_scale_f * fmaf((float)kk[4], pin[0], (float)kk[5] * pin[1]);
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            kq[c] = (float)kk[c];
+            kq[c] = fmaf(a.s2_f, pin[c], (float)kk[c]);
             kp[c] = a.dp_scale_f * (float)kk[3 + c];
         }
     }
@@ -288,6 +290,8 @@ StageArgs base_args(const ep_params& P, const AllPairsBufs& b, const APConfig& c
     a.s_f = (float)ks.s;
     a.dp_scale = ks.dp_scale;
     a.dp_scale_f = (float)ks.dp_scale;
+    a.s2 = P.inexact;
+    a.s2_f = (float)P.inexact;
     a.c0 = b.c0;
     a.x = b.x;
     a.acc = b.acc;

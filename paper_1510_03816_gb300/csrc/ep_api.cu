@@ -120,6 +120,10 @@ ep_status check_params(const ep_params* p)
     if (p->neigh < EP_AUTO || p->neigh > EP_CELLLIST) return set_error("unknown neigh %d", p->neigh), EP_EINVAL;
     if (p->neigh == EP_CELLLIST && p->kernel != EP_TENT)
         return set_error("the cell list needs the compactly supported tent kernel"), EP_EINVAL;
+    if (!(p->inexact >= 0.0) || !isfinite(p->inexact))
+        return set_error("inexact (sigma_n^2) must be finite and >= 0"), EP_EINVAL;
+    if (p->inexact != 0.0 && p->neigh == EP_CELLLIST)
+        return set_error("the inexact system runs on the all-pairs path"), EP_EINVAL;
     return EP_OK;
 }
 
@@ -272,8 +276,8 @@ bool use_celllist(const ep_params& P, int64_t n)
     if (P.kernel != EP_TENT) return false;
     if (P.neigh == EP_CELLLIST) return true;
     if (P.neigh == EP_ALLPAIRS) return false;
-    // EP_AUTO: the cell list (2-D, mixed precision) for large tent problems
-    return P.dim == 2 && P.precision == EP_MIXED && n >= 16384;
+    // EP_AUTO: the cell list (2-D, mixed precision) for large tent problems of the exact system
+    return P.dim == 2 && P.precision == EP_MIXED && P.inexact == 0.0 && n >= 16384;
 }
 
 // Problem state of one forward pass, whichever neighbour path it uses.
@@ -505,7 +509,7 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         return EP_OK;
     }
     // small 2-D mixed problems: the whole feedback loop on one CTA (no grid-wide sync per stage)
-    if (P.precision == EP_MIXED && P.dim == 2 && !use_celllist(P, n) && n <= kSmallMatchMaxN) {
+    if (P.precision == EP_MIXED && P.dim == 2 && !use_celllist(P, n) && n <= kSmallMatchMaxN && P.inexact == 0.0) {
         ep_status s = match_small(params, n, X, Y, p0, info, stream);
         if (s == EP_ENOTCONVERGED)
             set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", info->iters, info->resid_inf, info->eps);
@@ -581,11 +585,13 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
             else info->hist[k] = res;
         }
         if (!finite) { status = EP_EDIVERGED; break; }
-        if (res < info->eps) { status = EP_OK; break; }
+        if (P.inexact == 0.0 && res < info->eps) { status = EP_OK; break; }
         if (k == info->maxit) { status = EP_ENOTCONVERGED; break; }
         count_launch();
-    k_momentum_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(sp.dev, sY.dev, Q1, m, h);
+        k_momentum_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(sp.dev, sY.dev, Q1, m, h);
         ++k;
+        // the inexact system (Sec. 6) stops on the change of the momenta: |h (Y - Q(1))|_inf
+        if (P.inexact != 0.0 && h * res < info->eps) { status = EP_OK; break; }
     }
     info->iters = k;
     info->resid_inf = res;

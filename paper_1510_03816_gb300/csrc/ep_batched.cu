@@ -483,6 +483,7 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     for (int b = 0; b < nprob; ++b) {
         const ep_params& P = params[b];
         EP_TRY(check_params(&P));
+        if (P.inexact != 0.0) return set_error("ep_match_batched solves the exact system"), EP_EINVAL;
         if (P.dim != 2) return set_error("ep_match_batched: problem %d: dim must be 2", b), EP_EINVAL;
         if (P.precision != EP_MIXED)
             return set_error("ep_match_batched: problem %d: the batched path runs in mixed precision", b), EP_EINVAL;

@@ -335,6 +335,7 @@ ep_status flow_common(const ep_params* params, int64_t n, const double* q, const
         return set_error("%s: bad n or m", name), EP_EINVAL;
     const ep_params& P = *params;
     if (P.neigh == EP_CELLLIST) return set_error("%s: runs on the all-pairs path", name), EP_EINVAL;
+    if (P.inexact != 0.0) return set_error("%s: built for the exact system", name), EP_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (m == 0) return EP_OK;
     if (!x0 || !x1 || (n > 0 && (!q || !p))) return set_error("%s: NULL array", name), EP_EINVAL;

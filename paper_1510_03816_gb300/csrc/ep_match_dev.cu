@@ -34,6 +34,7 @@ constexpr int kMatchThreads = 256;
 struct MatchArgs {
     int n, steps, maxit;
     double sigma, dt, eps, h;  // h <= 0: default gain, computed in the kernel
+    double s2;                 // sigma_n^2 of the inexact system (Sec. 6), 0 for the exact one
     const double* X;
     const double* Y;
     double* p0;                // in: initial momenta, out: the last iterate
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
         }
         if (threadIdx.x == 0 && r1 > r0) atomicMax(a.red, mx);
         if (!grid_barrier(a.bar, a.err, ++epoch)) return;
-        const double m = bitsd(ld_acquire_u64(a.red));
+        const double m = bitsd(ld_acquire_u64(a.red)) + a.s2;
         h = m > 0.0 ? 1.0 / m : 1.0;
     }
     int k = 0, status = EP_ENOTCONVERGED;
@@ -196,6 +197,8 @@ __global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
                         double kv = kk[0];
 #pragma unroll
                         for (int u = 1; u < S2; ++u) kv = c == u ? kk[u] : kv;
+                        // dq + sigma_n^2 p_i for the inexact system (Sec. 6)
+                        if (c < DIM) kv += a.s2 * __ldcg(Din + (size_t)i * S2 + DIM + c);
                         double* xs = c < DIM ? a.x + (size_t)i * DIM + c : a.x + nd + (size_t)i * DIM + (c - DIM);
                         double* A = a.acc + (size_t)i * S2 + c;
                         if (stage < 3) {
@@ -227,12 +230,14 @@ __global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
         res = finite ? bitsd(rb) : __longlong_as_double(0x7FF8000000000000ll);
         if (a.hist && blockIdx.x == 0 && threadIdx.x == 0) a.hist[k] = res;
         if (!finite) { status = EP_EDIVERGED; break; }
-        if (res < a.eps) { status = EP_OK; break; }
+        if (a.s2 == 0.0 && res < a.eps) { status = EP_OK; break; }
         if (k == a.maxit) { status = EP_ENOTCONVERGED; break; }
         for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
             const size_t e = (size_t)r0 * DIM + t;
             a.p0[e] += h * (a.Y[e] - a.x[e]);
         }
+        // the inexact system (Sec. 6) stops on the change of the momenta, |h (Y - Q(1))|_inf
+        if (a.s2 != 0.0 && h * res < a.eps) { ++k; status = EP_OK; break; }
     }
     // H(X, p0) = 1/2 sum_i p_i . sum_j G_ij p_j (Eq. H) of the returned momenta
     for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
@@ -312,6 +317,7 @@ ep_status match_device_fp64(const ep_params& P, int64_t n, const double* X, cons
     a.dt = P.t1 / P.steps;
     a.eps = info->eps;
     a.h = info->h;
+    a.s2 = P.inexact;
     a.X = X;
     a.Y = Y;
     a.p0 = p0;

@@ -46,7 +46,7 @@ class EPError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("kernel", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("steps", ctypes.c_int), ("t1", ctypes.c_double), ("precision", ctypes.c_int),
-                ("neigh", ctypes.c_int)]
+                ("neigh", ctypes.c_int), ("inexact", ctypes.c_double)]
 
 
 class MatchInfo(ctypes.Structure):
@@ -149,8 +149,10 @@ def _check(status: int, allowed=(OK,)) -> int:
 
 
 def params(dim: int = 2, kernel: int = GAUSS, sigma: float = 0.1, steps: int = 100, t1: float = 1.0,
-           precision: int = MIXED, neigh: int = AUTO) -> Params:
-    return Params(int(dim), int(kernel), float(sigma), int(steps), float(t1), int(precision), int(neigh))
+           precision: int = MIXED, neigh: int = AUTO, inexact: float = 0.0) -> Params:
+    """ep_params; inexact = sigma_n^2 of the inexact particle system (0: exact)."""
+    return Params(int(dim), int(kernel), float(sigma), int(steps), float(t1), int(precision), int(neigh),
+                  float(inexact))
 
 
 # ------------------------------------------------------------------ array marshalling
@@ -273,6 +275,12 @@ def hamiltonian(q, p, prm: Params) -> float:
     return out.value
 
 
+def _shoots(prm: Params, info: MatchInfo, status: int) -> int:
+    """Shoots of a matching: iters + 1, except that the inexact system's loop (Sec. 6)
+    ends on an update when it converges."""
+    return info.iters if (prm.inexact != 0.0 and status == OK) else info.iters + 1
+
+
 def match(X, Y, prm: Params, h: float = 0.0, eps: float = 1e-6, maxit: int = 200, p0=None,
           hist: bool = True) -> MatchResult:
     """ep_match: Algorithm 1 with M = h I on the momenta.  p0=None starts from zero."""
@@ -298,7 +306,7 @@ def match(X, Y, prm: Params, h: float = 0.0, eps: float = 1e-6, maxit: int = 200
                          _stream_for(X))
     _check(st, allowed=(OK, ENOTCONVERGED, EDIVERGED))
     return MatchResult(p, st, info.iters, info.resid_inf, info.H, info.h,
-                       hbuf[: info.iters + 1] if hist else None)
+                       hbuf[: _shoots(prm, info, st)] if hist else None)
 
 
 def hvp(q, p, vq, vp, prm: Params):
