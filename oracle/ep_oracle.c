@@ -25,7 +25,10 @@
  *     and the transport of points by the flow it generates along a shoot
  *     (the deformation phi_t with d phi_t(x)/dt = u(phi_t(x), t))
  *   - the inexact particle system, its shoot and its matching loop with the
- *     momentum-difference stop                           (Sec. 6, Eq. N-particle-inexact).
+ *     momentum-difference stop                           (Sec. 6, Eq. N-particle-inexact)
+ *   - the tangent-linear RK4 shoot (directional derivative of the shooting
+ *     map), the building block of the Newton-type gain M = h (D phi)^-1 of
+ *     Sec. 5 (Theorem 1).
  *
  * Parity pins (tests/test_oracle_pins.py): every function here is checked
  * against something other than itself -- finite differences of H, closed
@@ -501,6 +504,66 @@ void orc_hvp(int dim, int kernel, double sigma, long n, const double* q, const d
             hp[i * dim + c] = ap[c];
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tangent-linear shoot: the derivative of the RK4 shoot (Q(1), P(1)) at     */
+/* (q0, p0) along (vq0, vp0), obtained by differentiating each RK4 stage.    */
+/* With F = (dH/dp, -dH/dq) (Eq. N-particle) its Jacobian acts as            */
+/*   J_F(y) v = ( (d2H v)_p , -(d2H v)_q )          (d2H: Hessian of Eq. H)  */
+/* and a step is                                                             */
+/*   dk1 = J_F(x) dx,          dk2 = J_F(y2) (dx + dt/2 dk1),                */
+/*   dk3 = J_F(y3) (dx + dt/2 dk2),  dk4 = J_F(y4) (dx + dt dk3),            */
+/*   dx <- dx + dt/6 (dk1 + 2 dk2 + 2 dk3 + dk4),                            */
+/* at the stage states y_s of the primal step, which is advanced alongside.  */
+/* ------------------------------------------------------------------------ */
+int orc_shoot_tangent(int dim, int kernel, double sigma, int steps, double t1, long n, const double* q0,
+                      const double* p0, const double* vq0, const double* vp0, double* q1, double* p1,
+                      double* vq1, double* vp1)
+{
+    if (dim < 1 || dim > 3 || steps < 1 || n < 0) return ORC_EINVAL;
+    long a, m = n * dim;
+    double* w = (double*)malloc(sizeof(double) * (size_t)(24 * m + 1));
+    if (!w) return ORC_EINVAL;
+    double *kq[4], *kp[4], *dkq[4], *dkp[4];
+    for (int s = 0; s < 4; ++s) {
+        kq[s] = w + (4 * s + 0) * m;
+        kp[s] = w + (4 * s + 1) * m;
+        dkq[s] = w + (4 * s + 2) * m;
+        dkp[s] = w + (4 * s + 3) * m;
+    }
+    double *yq = w + 16 * m, *yp = w + 17 * m, *dyq = w + 18 * m, *dyp = w + 19 * m;
+    double *hq = w + 20 * m, *hp = w + 21 * m;
+    memcpy(q1, q0, sizeof(double) * (size_t)m);
+    memcpy(p1, p0, sizeof(double) * (size_t)m);
+    memcpy(vq1, vq0, sizeof(double) * (size_t)m);
+    memcpy(vp1, vp0, sizeof(double) * (size_t)m);
+    const double dt = t1 / steps;
+    const double c[4] = {0.0, 0.5, 0.5, 1.0};  /* stage s input: x + c_s dt k_{s-1} */
+    for (int st = 0; st < steps; ++st) {
+        for (int s = 0; s < 4; ++s) {
+            for (a = 0; a < m; ++a) {
+                yq[a] = s == 0 ? q1[a] : q1[a] + c[s] * dt * kq[s - 1][a];
+                yp[a] = s == 0 ? p1[a] : p1[a] + c[s] * dt * kp[s - 1][a];
+                dyq[a] = s == 0 ? vq1[a] : vq1[a] + c[s] * dt * dkq[s - 1][a];
+                dyp[a] = s == 0 ? vp1[a] : vp1[a] + c[s] * dt * dkp[s - 1][a];
+            }
+            orc_rhs(dim, kernel, sigma, n, yq, yp, kq[s], kp[s]);
+            orc_hvp(dim, kernel, sigma, n, yq, yp, dyq, dyp, hq, hp);
+            for (a = 0; a < m; ++a) {
+                dkq[s][a] = hp[a];
+                dkp[s][a] = -hq[a];
+            }
+        }
+        for (a = 0; a < m; ++a) {
+            q1[a] += dt / 6.0 * (kq[0][a] + 2.0 * kq[1][a] + 2.0 * kq[2][a] + kq[3][a]);
+            p1[a] += dt / 6.0 * (kp[0][a] + 2.0 * kp[1][a] + 2.0 * kp[2][a] + kp[3][a]);
+            vq1[a] += dt / 6.0 * (dkq[0][a] + 2.0 * dkq[1][a] + 2.0 * dkq[2][a] + dkq[3][a]);
+            vp1[a] += dt / 6.0 * (dkp[0][a] + 2.0 * dkp[1][a] + 2.0 * dkp[2][a] + dkp[3][a]);
+        }
+    }
+    free(w);
+    return ORC_OK;
 }
 
 /* Transposed Jacobian of F = (dH/dp, -dH/dq) applied to w = (wq, wp):       */

@@ -96,6 +96,8 @@ def _load():
         lib.orc_shoot_inexact.argtypes = [i, i, d, d, i, d, l, p, p, p, p]
         lib.orc_match_inexact.restype = i
         lib.orc_match_inexact.argtypes = [i, i, d, d, i, d, l, p, p, d, d, i, p, p, p, p]
+        lib.orc_shoot_tangent.restype = i
+        lib.orc_shoot_tangent.argtypes = [i, i, d, i, d, l, p, p, p, p, p, p, p, p]
         lib.orc_set_threads.restype = None
         lib.orc_set_threads.argtypes = [i]
         lib.orc_max_threads.restype = i
@@ -338,3 +340,56 @@ def match_inexact(X, Y, kernel: int, sigma: float, s2: float, steps: int, h: flo
         raise ValueError("orc_match_inexact: invalid arguments")
     shoots = it.value if st == OK else it.value + 1  # a converged loop ends on an update
     return p, st, it.value, res.value, hist[:shoots]
+
+
+def shoot_tangent(q0, p0, vq0, vp0, kernel: int, sigma: float, steps: int, t1: float = 1.0):
+    """Derivative of the RK4 shoot at (q0, p0) along (vq0, vp0): returns (Q1, P1, dQ1, dP1)."""
+    q0 = _arr(q0)
+    dim = q0.shape[1]
+    p0, vq0, vp0 = _arr(p0, dim), _arr(vq0, dim), _arr(vp0, dim)
+    q1, p1, vq1, vp1 = (np.empty_like(q0) for _ in range(4))
+    if _load().orc_shoot_tangent(dim, kernel, sigma, steps, t1, q0.shape[0], _ptr(q0), _ptr(p0), _ptr(vq0),
+                                 _ptr(vp0), _ptr(q1), _ptr(p1), _ptr(vq1), _ptr(vp1)) != 0:
+        raise ValueError("orc_shoot_tangent: invalid arguments")
+    return q1, p1, vq1, vp1
+
+
+def shooting_jacobian(X, p0, kernel: int, sigma: float, steps: int, t1: float = 1.0):
+    """D phi = dQ(1)/dp0 (n d x n d, row-major flattening), one tangent shoot per column."""
+    X = _arr(X)
+    n, dim = X.shape
+    p0 = _arr(p0, dim)
+    J = np.empty((n * dim, n * dim))
+    zero = np.zeros_like(X)
+    for a in range(n * dim):
+        e = np.zeros(n * dim)
+        e[a] = 1.0
+        J[:, a] = shoot_tangent(X, p0, zero, e.reshape(n, dim), kernel, sigma, steps, t1)[2].ravel()
+    return J
+
+
+def match_newton(X, Y, kernel: int, sigma: float, steps: int, h: float = 1.0, eps: float = 1e-6,
+                 maxit: int = 50, p0=None, t1: float = 1.0):
+    """Algorithm 1 with the Newton-type gain of Sec. 5: p0 <- p0 + h (D phi)^-1 (Y - Q(1)),
+    D phi from tangent shoots and solved directly (a library LU).  Stopping as Algorithm 1;
+    returns (p0, status, iters, resid, hist)."""
+    X = _arr(X)
+    n, dim = X.shape
+    Y = _arr(Y, dim)
+    p = np.zeros_like(X) if p0 is None else _arr(p0, dim).copy()
+    hist = []
+    k = 0
+    while True:
+        q1, _ = shoot(X, p, kernel, sigma, steps, t1)
+        r = Y - q1
+        res = float(np.abs(r).max()) if np.all(np.isfinite(r)) else float("nan")
+        hist.append(res)
+        if not np.isfinite(res):
+            return p, EDIVERGED, k, res, np.array(hist)
+        if res < eps:
+            return p, OK, k, res, np.array(hist)
+        if k == maxit:
+            return p, ENOTCONVERGED, k, res, np.array(hist)
+        J = shooting_jacobian(X, p, kernel, sigma, steps, t1)
+        p = p + h * np.linalg.solve(J, r.ravel()).reshape(n, dim)
+        k += 1

@@ -46,6 +46,9 @@ MUTANTS = {
                           "for (long a = 0; a < n * dim; ++a) dq[a] -= s2 * p[a];"),
     "inexact_stop_on_residual": ("if (fabs(d) > dmax) dmax = fabs(d);",
                                  "if (fabs(d) / h > dmax) dmax = fabs(d) / h;"),
+    "tangent_dp_sign": ("                dkp[s][a] = -hq[a];", "                dkp[s][a] = hq[a];"),
+    "tangent_at_step_start": ("            orc_hvp(dim, kernel, sigma, n, yq, yp, dyq, dyp, hq, hp);",
+                              "            orc_hvp(dim, kernel, sigma, n, q1, p1, dyq, dyp, hq, hp);"),
     "flow_stale_velocity_stage": ("orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k4x);",
                                   "orc_velocity(dim, kernel, sigma, n, q1, p1, m, yx, k4x);"),
 }

@@ -512,3 +512,53 @@ def test_inexact_match_stops_on_the_momentum_difference():
     p, st, it, res, hist = o.match_inexact(X, Y, o.GAUSS, 0.1, s2, 3, eps=eps, maxit=500)
     np.testing.assert_allclose(p, c, rtol=0, atol=1e-15)  # h = 1 / (1 + s2): exact after one update
     assert st == o.OK and it == 2
+
+
+# --------------------------------------------------------------------------- tangent-linear shoot and the Newton gain (Sec. 5)
+
+
+@pytest.mark.parametrize("kernel,sigma", KERNELS)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tangent_shoot_matches_central_differences(kernel, sigma, dim):
+    q, p = _cloud(8, dim, seed=60 + dim + kernel, spread=0.8, pscale=0.2, min_gap=0.05, sigma=sigma, kernel=kernel)
+    rng = np.random.default_rng(61)
+    vq, vp = rng.normal(size=q.shape), rng.normal(size=q.shape)
+    steps, eps = 6, 1e-6
+    q1, p1, dq1, dp1 = o.shoot_tangent(q, p, vq, vp, kernel, sigma, steps)
+    qa, pa = o.shoot(q + eps * vq, p + eps * vp, kernel, sigma, steps)
+    qb, pb = o.shoot(q - eps * vq, p - eps * vp, kernel, sigma, steps)
+    scale = max(1.0, np.abs(dq1).max(), np.abs(dp1).max())
+    assert np.abs((qa - qb) / (2 * eps) - dq1).max() < 1e-7 * scale
+    assert np.abs((pa - pb) / (2 * eps) - dp1).max() < 1e-7 * scale
+    # the primal part is the plain shoot, bit for bit
+    qs, ps = o.shoot(q, p, kernel, sigma, steps)
+    np.testing.assert_array_equal(q1, qs)
+    np.testing.assert_array_equal(p1, ps)
+
+
+def test_tangent_shoot_is_linear_in_the_direction():
+    q, p = _cloud(10, 2, seed=62, spread=0.7, pscale=0.2, min_gap=0.02)
+    rng = np.random.default_rng(63)
+    v1, v2 = rng.normal(size=q.shape), rng.normal(size=q.shape)
+    z = np.zeros_like(q)
+    a = o.shoot_tangent(q, p, z, v1, o.GAUSS, 0.3, 7)[2]
+    b = o.shoot_tangent(q, p, z, v2, o.GAUSS, 0.3, 7)[2]
+    c = o.shoot_tangent(q, p, z, 2.0 * v1 - 3.0 * v2, o.GAUSS, 0.3, 7)[2]
+    np.testing.assert_allclose(c, 2.0 * a - 3.0 * b, rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(o.shoot_tangent(q, p, z, z, o.GAUSS, 0.3, 7)[2], 0.0)
+
+
+def test_newton_gain_one_particle_and_quadratic_convergence():
+    # one Gaussian particle: Q(1) = X + p0, D phi = I, so one full Newton step lands exactly
+    X, Y = np.array([[0.3, 0.4]]), np.array([[0.35, 0.42]])
+    p, st, it, res, hist = o.match_newton(X, Y, o.GAUSS, 0.2, 5, h=1.0, eps=1e-13)
+    assert st == o.OK and it == 1 and res < 1e-15
+    np.testing.assert_allclose(p, Y - X, rtol=0, atol=1e-16)
+    # a 12-landmark circle -> ellipse (Gaussian sigma = 0.1, D phi well conditioned): the
+    # residual squares from one iterate to the next
+    pr = w.circle_to_ellipse(12, sigma=0.1, kernel=o.GAUSS, steps=10)
+    p, st, it, res, hist = o.match_newton(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=1.0, eps=1e-12, maxit=20)
+    assert st == o.OK and it <= 6
+    r = np.array(hist)
+    assert np.all(r[1:] < r[:-1])
+    assert np.all(r[2:] < 50.0 * r[1:-1] ** 2)
