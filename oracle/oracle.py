@@ -393,3 +393,42 @@ def match_newton(X, Y, kernel: int, sigma: float, steps: int, h: float = 1.0, ep
         J = shooting_jacobian(X, p, kernel, sigma, steps, t1)
         p = p + h * np.linalg.solve(J, r.ravel()).reshape(n, dim)
         k += 1
+
+
+def gram(X, kernel: int, sigma: float):
+    """G(X): the n x n matrix of kernel values G(|X_i - X_j|) (Eq. u at t = 0 is u = G(X) p)."""
+    X = _arr(X)
+    n = X.shape[0]
+    K = np.empty((n, n))
+    for i in range(n):
+        for j in range(n):
+            K[i, j] = G(kernel, sigma, float(np.sqrt(np.sum((X[i] - X[j]) ** 2))))
+    return K
+
+
+def match_velocity(X, Y, kernel: int, sigma: float, steps: int, h: float = 1.0, eps: float = 1e-6,
+                   maxit: int = 200, p0=None, t1: float = 1.0):
+    """Algorithm 1 with the update applied to the velocity (steps 3 and 4): u0 = G(X) p0 is
+    corrected by u0 += h (Y - Q(1)) and the momenta recovered from it, p0 = G(X)^-1 u0, i.e.
+    p0 <- p0 + h G(X)^-1 (Y - Q(1)) (a library LU per component).  Stopping as Algorithm 1;
+    returns (p0, status, iters, resid, hist)."""
+    X = _arr(X)
+    n, dim = X.shape
+    Y = _arr(Y, dim)
+    p = np.zeros_like(X) if p0 is None else _arr(p0, dim).copy()
+    GX = gram(X, kernel, sigma)
+    hist = []
+    k = 0
+    while True:
+        q1, _ = shoot(X, p, kernel, sigma, steps, t1)
+        r = Y - q1
+        res = float(np.abs(r).max()) if np.all(np.isfinite(r)) else float("nan")
+        hist.append(res)
+        if not np.isfinite(res):
+            return p, EDIVERGED, k, res, np.array(hist)
+        if res < eps:
+            return p, OK, k, res, np.array(hist)
+        if k == maxit:
+            return p, ENOTCONVERGED, k, res, np.array(hist)
+        p = p + h * np.linalg.solve(GX, r)
+        k += 1

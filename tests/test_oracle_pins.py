@@ -562,3 +562,56 @@ def test_newton_gain_one_particle_and_quadratic_convergence():
     r = np.array(hist)
     assert np.all(r[1:] < r[:-1])
     assert np.all(r[2:] < 50.0 * r[1:-1] ** 2)
+
+
+# --------------------------------------------------------------------------- velocity update rule (Algorithm 1 steps 3-4)
+
+
+def test_gram_matrix_is_the_velocity_at_the_landmarks():
+    # Eq. u at t = 0 and at the landmarks themselves: u(X) = G(X) p
+    q, p = _cloud(9, 2, seed=70, spread=0.8, min_gap=0.03, sigma=0.45, kernel=o.TENT)
+    for kernel, sigma in KERNELS:
+        GX = o.gram(q, kernel, sigma)
+        np.testing.assert_array_equal(GX, GX.T)
+        np.testing.assert_array_equal(np.diag(GX), 1.0)
+        np.testing.assert_allclose(GX @ p, o.velocity(q, p, q, kernel, sigma), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("kernel,sigma", [(o.TENT, 0.45), (o.EXPCONE, 0.4), (o.GAUSS, 0.15)])
+def test_velocity_rule_inverts_the_linearised_shoot(kernel, sigma):
+    # For a small displacement Y = X + e V the shoot is Q(1) = X + G(X) p0 + O(|p0|^2), so one
+    # velocity-rule update from p0 = 0 with h = 1 leaves an O(e^2) residual: the ratio of the
+    # two residuals falls in proportion to e.  The momentum rule only damps it by a constant.
+    rng = np.random.default_rng(71)
+    X = rng.uniform(0, 1, (10, 2))
+    V = rng.normal(size=X.shape)
+    ratios = []
+    for e in (1e-3, 1e-4):
+        hist = o.match_velocity(X, X + e * V, kernel, sigma, 8, h=1.0, eps=0.0, maxit=1)[4]
+        ratios.append(hist[1] / hist[0])
+        hm = o.match(X, X + e * V, kernel, sigma, 8, h=0.0, eps=0.0, maxit=1)[4]
+        assert hm[1] / hm[0] > 0.5
+    assert ratios[0] < 0.05
+    assert 0.08 < ratios[1] / ratios[0] < 0.12
+
+
+def test_velocity_rule_equals_momentum_rule_when_the_gram_matrix_is_identity():
+    # landmarks farther apart than the tent's support: G(X) = I and the two rules coincide
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.2]])
+    Y = X + np.array([[0.1, -0.05], [0.02, 0.08], [-0.06, 0.03], [0.04, 0.04]])
+    np.testing.assert_array_equal(o.gram(X, o.TENT, 0.5), np.eye(4))
+    a = o.match_velocity(X, Y, o.TENT, 0.5, 6, h=0.6, eps=1e-12, maxit=40)
+    b = o.match(X, Y, o.TENT, 0.5, 6, h=0.6, eps=1e-12, maxit=40)
+    assert a[1] == b[1] and a[2] == b[2]
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[4], b[4])
+
+
+def test_velocity_rule_converges_on_a_noise_free_tent_problem():
+    # circle -> ellipse with the tent (noise-free target): with h = 1/2 the velocity rule
+    # contracts the residual at a steady linear rate near 1 - h (G(X)^-1 D phi is near I)
+    pr = w.circle_to_ellipse(16, sigma=0.45, kernel=o.TENT, steps=20)
+    p, st, it, res, hist = o.match_velocity(pr.X, pr.Y, o.TENT, 0.45, 20, h=0.5, eps=1e-8, maxit=80)
+    assert st == o.OK and it < 60
+    r = np.array(hist)
+    assert np.all(r[-5:] / r[-6:-1] < 0.7)
