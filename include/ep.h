@@ -54,6 +54,18 @@ typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
 /* EP_AUTO picks the cell list for EP_TENT when it pays off, else all-pairs. */
 typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
 
+/* Update rule of ep_match (Algorithm 1 step 3-4 and Sec. 5), r = Y - Q(1):
+ *  EP_RULE_MOMENTUM  p0 += h r                 M = h I applied to the momenta (default)
+ *  EP_RULE_VELOCITY  p0 += h G(X)^-1 r         the velocity u = G(X) p0 (Eq. u at t = 0)
+ *                                              is updated by u += h r and p0 recovered
+ *                                              from u (Algorithm 1 step 4)
+ *  EP_RULE_NEWTON    p0 += h (D phi)^-1 r      the gain M = h (D phi)^-1 of Theorem 1,
+ *                                              D phi = dQ(1)/dp0 of the RK4 shoot
+ * The two solved rules run restarted GMRES (ep_match_info.krylov vectors) whose
+ * products are the all-pairs Gram product G(X) v (velocity) or a tangent-linear
+ * shoot along (0, v) (Newton); they are FP64, all-pairs, exact system only. */
+typedef enum { EP_RULE_MOMENTUM = 0, EP_RULE_VELOCITY = 1, EP_RULE_NEWTON = 2 } ep_rule;
+
 typedef struct {
     int dim;        /* 2 or 3 */
     int kernel;     /* ep_kernel */
@@ -82,6 +94,11 @@ typedef struct {
     double H;        /* out: Hamiltonian H(X, p0) of Eq. H for the returned p0 */
     double* hist;    /* in, optional: maxit + 1 doubles (host or device) that receive the
                         residual of every shoot; NULL for none */
+    int rule;        /* in: ep_rule (0 = EP_RULE_MOMENTUM).  For the solved rules h <= 0
+                        means h = 1; ep_match_batched requires EP_RULE_MOMENTUM */
+    int krylov;      /* in: GMRES restart length of the solved rules (0 = min(n dim, 200));
+                        the inner solve stops at relative residual 1e-12 or after 4 krylov
+                        products */
 } ep_match_info;
 
 /* Right-hand side of the N-particle system (Sec. 3.1, Eq. N-particle):
@@ -109,6 +126,16 @@ ep_status ep_shoot(const ep_params* params, int64_t n, const double* q0, const d
  * EP_ENOTCONVERGED or EP_EDIVERGED; info is filled in all three cases. */
 ep_status ep_match(const ep_params* params, int64_t n, const double* X, const double* Y,
                    double* p0, ep_match_info* info, void* stream);
+
+/* Tangent-linear shoot (Sec. 5, the derivative D phi of the shooting map): the RK4
+ * shoot of ep_shoot from (q0, p0) differentiated along (vq0, vp0); each stage
+ * applies the Jacobian of Eq. N-particle's right-hand side, (d2H v)_p and -(d2H v)_q
+ * of Eq. H, at the recorded stage state.  Outputs q1, p1 (the shoot, may be NULL) and
+ * vq1, vp1 = d(Q(1), P(1)) along (vq0, vp0), all (n, dim).  FP64, all-pairs, exact
+ * system (EP_EINVAL otherwise).  Synchronises the stream. */
+ep_status ep_shoot_tangent(const ep_params* params, int64_t n, const double* q0, const double* p0,
+                           const double* vq0, const double* vp0, double* q1, double* p1, double* vq1,
+                           double* vp1, void* stream);
 
 /* Gradient of the inexact-matching energy (Sec. 6, Eq. inexact-E, written with
  * Eq. E=2H):  E(p0) = 1/2 p0^T G(X) p0 + lambda/2 ||Q(1) - Y||^2  with respect to

@@ -501,6 +501,8 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     const ep_params& P = *params;
     cudaStream_t st = as_stream(stream);
     const size_t m = (size_t)n * P.dim;
+    if (info->rule < EP_RULE_MOMENTUM || info->rule > EP_RULE_NEWTON)
+        return set_error("ep_match: unknown update rule %d", info->rule), EP_EINVAL;
     info->iters = 0;
     info->resid_inf = 0.0;
     info->H = 0.0;
@@ -508,6 +510,8 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         if (info->h <= 0.0) info->h = 1.0;
         return EP_OK;
     }
+    // the solved update rules (velocity, Newton): host GMRES over device products
+    if (info->rule != EP_RULE_MOMENTUM) return rule_match(P, n, X, Y, p0, info, st);
     // small 2-D mixed problems: the whole feedback loop on one CTA (no grid-wide sync per stage)
     if (P.precision == EP_MIXED && P.dim == 2 && !use_celllist(P, n) && n <= kSmallMatchMaxN && P.inexact == 0.0) {
         ep_status s = match_small(params, n, X, Y, p0, info, stream);
@@ -607,6 +611,13 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     if (status == EP_ENOTCONVERGED) set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", k, res, info->eps);
     if (status == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", k);
     return status;
+}
+
+ep_status ep_shoot_tangent(const ep_params* params, int64_t n, const double* q0, const double* p0,
+                           const double* vq0, const double* vp0, double* q1, double* p1, double* vq1, double* vp1,
+                           void* stream)
+{
+    return tangent_entry(params, n, q0, p0, vq0, vp0, q1, p1, vq1, vp1, as_stream(stream));
 }
 
 ep_status ep_hvp(const ep_params* params, int64_t n, const double* q, const double* p, const double* vq,

@@ -495,6 +495,8 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
             return set_error("ep_match_batched: internal size limit"), EP_EINVAL;
         const ep_match_info& I = infos[b];
         if (I.maxit < 0 || !(I.eps >= 0.0)) return set_error("ep_match_batched: problem %d: bad maxit/eps", b), EP_EINVAL;
+        if (I.rule != EP_RULE_MOMENTUM)
+            return set_error("ep_match_batched: problem %d: only the momentum update rule is batched", b), EP_EINVAL;
         const KernelScale ks = kernel_scale(P.kernel, P.sigma);
         BProb& q = probs[b];
         q.off = offsets[b];

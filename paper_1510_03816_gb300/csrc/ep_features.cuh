@@ -47,6 +47,12 @@ size_t match_device_bytes(int64_t n, int dim, int maxit);
 ep_status match_device_fp64(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
                             ep_match_info* info, double* hist_dev, Arena* ar, cudaStream_t st, double out[5]);
 constexpr int64_t kDeviceMatchMaxN = 16384;
+
+// Tangent-linear shoot and the solved update rules of ep_match (ep_newton.cu).
+ep_status tangent_entry(const ep_params* params, int64_t n, const double* q0, const double* p0, const double* vq0,
+                        const double* vp0, double* q1, double* p1, double* vq1, double* vp1, void* stream);
+ep_status rule_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
+                     ep_match_info* info, cudaStream_t st);
 constexpr int64_t kSmallMatchMaxN = 384;
 
 }  // namespace ep

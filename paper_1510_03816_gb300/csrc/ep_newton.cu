@@ -1,0 +1,560 @@
+// ep_newton.cu -- the tangent-linear RK4 shoot (the directional derivative of
+// the shooting map p0 -> (Q(1), P(1))) and Algorithm 1 with the Newton-type gain
+// M = h (D phi)^-1 of Sec. 5 (Theorem 1), plain FP64 method.
+//
+// Tangent-linear shoot.  The primal shoot is run once with every RK4 stage input
+// recorded.  With F = (dH/dp, -dH/dq) of Eq. N-particle, a stage's derivative is
+//   J_F(y) v = ( sum_j [G_ij dp_j + phi_ij (d_ij . dd_ij) p_j] ,
+//               -sum_{j != i} [(dp_i . p_j + p_i . dp_j) phi_ij d_ij
+//                              + (p_i . p_j)(phi_ij dd_ij + psi_ij (d_ij . dd_ij) d_ij)] )
+// (the two blocks of the Hessian of Eq. H, d_ij = q_i - q_j, dd_ij = dq_i - dq_j),
+// and the tangent follows the primal RK4 stage by stage:
+//   dk_s = J_F(y_s) dy_s,  dy_{s+1} = dx_n + c_{s+1} dt dk_s,
+//   dx_{n+1} = dx_n + dt/6 (dk_1 + 2 dk_2 + 2 dk_3 + dk_4).
+// One cooperative launch covers the whole tangent shoot: every CTA owns the
+// particles [c n / G, (c+1) n / G), sums their rows over all sources in FP64
+// against the recorded stage state, and applies the tangent RK4 stage; one grid
+// barrier per stage publishes the next tangent stage inputs.
+//
+// Newton gain.  Each iterate shoots (recording the stages), takes the max-norm
+// residual r = Y - Q(1) and stops as Algorithm 1 does; otherwise it solves
+// (D phi) delta = r by restarted GMRES whose matrix-vector products are tangent
+// shoots along (0, v) (matrix-free: D phi = dQ(1)/dp0 is never formed), and
+// updates p0 += h delta.  The Krylov basis lives on the host (n dim doubles per
+// vector); each product is one launch.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ep_allpairs_dev.cuh"
+#include "ep_features.cuh"
+
+namespace ep {
+
+namespace {
+
+constexpr int kTanThreads = 256;
+// relative residual at which the inner Krylov solve of a gained update stops
+constexpr double kKrylovTol = 1e-12;
+
+// FP64 kernel value, phi = G'(r)/r and psi = phi'(r)/r (unscaled): the
+// derivatives the Hessian of Eq. H needs.  Reciprocals of sigma are hoisted and
+// 1/r comes from rsqrt; the tent keeps r = sqrt(r2) for its support test.
+template <int KER>
+__device__ __forceinline__ void kfun3_f64(double r2, double sigma, double& G, double& phi, double& psi)
+{
+    const double is = 1.0 / sigma;
+    if constexpr (KER == EP_GAUSS) {
+        G = exp(-0.5 * (r2 * (is * is)));
+        phi = -G * (is * is);
+        psi = G * (is * is) * (is * is);
+    } else if constexpr (KER == EP_TENT) {
+        const double r = sqrt(r2);
+        const bool in = r < sigma && r2 > 0.0;
+        const double rs = r2 > 0.0 ? rsqrt(r2) : 0.0;
+        G = r < sigma ? 1.0 - r * is : 0.0;
+        phi = in ? -is * rs : 0.0;
+        psi = in ? is * rs * rs * rs : 0.0;
+    } else {
+        const double r = sqrt(r2);
+        const double rs = r2 > 0.0 ? rsqrt(r2) : 0.0;
+        G = exp(-r * is);
+        phi = r2 > 0.0 ? -G * is * rs : 0.0;
+        psi = r2 > 0.0 ? G * (is * is * rs * rs + is * rs * rs * rs) : 0.0;
+    }
+}
+
+struct TanArgs {
+    int n, steps;
+    double dt, sigma;
+    const double* drec;  // (4 steps + 1) primal stage copies, (q, p) = 2 dim doubles per particle
+    const double* v0;    // initial tangent [dq (n dim) | dp (n dim)]
+    double* dx;          // tangent state at the step start (2 dim per particle, own rows)
+    double* dacc;        // tangent RK4 accumulator dk1 + 2 dk2 + 2 dk3
+    double* T[2];        // tangent stage inputs (2 dim per particle), ping-pong
+    double* out;         // [dQ(1) (n dim) | dP(1) (n dim)]
+    unsigned* bar;
+    int* err;
+};
+
+// Sum of V doubles over the CTA; complete in every thread.
+template <int V>
+__device__ __forceinline__ void tan_cta_sum(double (&v)[V], double* sm)
+{
+    constexpr int W = kTanThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < V; ++k) sm[warp * V + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        double s = 0.0;
+        for (int w = 0; w < W; ++w) s += sm[w * V + k];
+        v[k] = s;
+    }
+}
+
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kTanThreads) k_tangent_fp64(TanArgs a)
+{
+    constexpr int S2 = 2 * DIM;
+    __shared__ double sm_d[(kTanThreads / 32) * S2];
+    const int n = a.n;
+    const int r0 = (int)((long long)blockIdx.x * n / gridDim.x), r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
+    const size_t nd = (size_t)n * DIM;
+    unsigned epoch = 0;
+    // dx = v0, first stage input T[0] = v0 (own particles)
+    for (int t = threadIdx.x; t < (r1 - r0) * S2; t += kTanThreads) {
+        const int i = r0 + t / S2, c = t % S2;
+        const double v = c < DIM ? a.v0[(size_t)i * DIM + c] : a.v0[nd + (size_t)i * DIM + (c - DIM)];
+        a.dx[(size_t)i * S2 + c] = v;
+        a.T[0][(size_t)i * S2 + c] = v;
+    }
+    if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+    int cur = 0;
+    for (int k = 0; k < a.steps; ++k) {
+        for (int s = 0; s < 4; ++s) {
+            const double* Y = a.drec + (size_t)(4 * k + s) * S2 * n;
+            const double* Tin = a.T[cur];
+            double* Tout = a.T[cur ^ 1];
+            for (int i = r0; i < r1; ++i) {
+                double qi[DIM], pi[DIM], vqi[DIM], vpi[DIM];
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) {
+                    qi[c] = __ldcg(Y + (size_t)i * S2 + c);
+                    pi[c] = __ldcg(Y + (size_t)i * S2 + DIM + c);
+                    vqi[c] = __ldcg(Tin + (size_t)i * S2 + c);
+                    vpi[c] = __ldcg(Tin + (size_t)i * S2 + DIM + c);
+                }
+                // h[0..DIM): (d2H v)_p block; h[DIM..2 DIM): (d2H v)_q block
+                double h[S2];
+#pragma unroll
+                for (int u = 0; u < S2; ++u) h[u] = 0.0;
+                for (int j = threadIdx.x; j < n; j += kTanThreads) {
+                    double d[DIM], dv[DIM], pj[DIM], vpj[DIM];
+                    double r2 = 0.0, ddv = 0.0, pp = 0.0, a1 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) {
+                        d[c] = qi[c] - __ldcg(Y + (size_t)j * S2 + c);
+                        dv[c] = vqi[c] - __ldcg(Tin + (size_t)j * S2 + c);
+                        pj[c] = __ldcg(Y + (size_t)j * S2 + DIM + c);
+                        vpj[c] = __ldcg(Tin + (size_t)j * S2 + DIM + c);
+                        r2 += d[c] * d[c];
+                        ddv += d[c] * dv[c];
+                        pp += pi[c] * pj[c];
+                        a1 += vpi[c] * pj[c] + pi[c] * vpj[c];
+                    }
+                    double G, phi, psi;
+                    kfun3_f64<KER>(r2, a.sigma, G, phi, psi);
+#pragma unroll
+                    for (int c = 0; c < DIM; ++c) h[c] += G * vpj[c] + phi * ddv * pj[c];
+                    if (j != i) {
+#pragma unroll
+                        for (int c = 0; c < DIM; ++c) h[DIM + c] += a1 * phi * d[c] + pp * (phi * dv[c] + psi * ddv * d[c]);
+                    }
+                }
+                tan_cta_sum<S2>(h, sm_d);
+                // dk = (h_p, -h_q); the tangent RK4 stage, one thread per component
+                if (threadIdx.x < S2) {
+                    const int c = threadIdx.x;
+                    double hc = h[0];
+#pragma unroll
+                    for (int u = 1; u < S2; ++u) hc = c == u ? h[u] : hc;
+                    const double dk = c < DIM ? hc : -hc;
+                    double* X = a.dx + (size_t)i * S2 + c;
+                    double* A = a.dacc + (size_t)i * S2 + c;
+                    if (s < 3) {
+                        const double cdt = (s == 2 ? 1.0 : 0.5) * a.dt;
+                        Tout[(size_t)i * S2 + c] = *X + cdt * dk;
+                        *A = s == 0 ? dk : *A + 2.0 * dk;
+                    } else {
+                        const double nv = *X + a.dt / 6.0 * (*A + dk);
+                        *X = nv;
+                        Tout[(size_t)i * S2 + c] = nv;
+                    }
+                }
+            }
+            cur ^= 1;
+            if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+        }
+    }
+    for (int t = threadIdx.x; t < (r1 - r0) * S2; t += kTanThreads) {
+        const int i = r0 + t / S2, c = t % S2;
+        const double v = a.dx[(size_t)i * S2 + c];
+        if (c < DIM)
+            a.out[(size_t)i * DIM + c] = v;
+        else
+            a.out[nd + (size_t)i * DIM + (c - DIM)] = v;
+    }
+}
+
+// Device buffers of one tangent-linear problem.
+struct TanBufs {
+    AllPairsBufs ap;
+    double* drec = nullptr;
+    double* dx = nullptr;
+    double* dacc = nullptr;
+    double* T[2] = {nullptr, nullptr};
+    double* v0 = nullptr;
+    double* out = nullptr;
+    unsigned* bar = nullptr;
+    int* err = nullptr;
+};
+
+size_t tan_bytes(int64_t n, int dim, int steps, bool rec = true)
+{
+    Sizer z;
+    const size_t m = (size_t)n * dim;
+    z.add(allpairs_bytes((int)n, dim, EP_FP64));
+    if (rec) z.add(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));  // recorded stages
+    for (int k = 0; k < 4; ++k) z.add(sizeof(double) * 2 * m);  // dx, dacc, T[2]
+    z.add(sizeof(double) * 2 * m * 2);                          // v0, out
+    z.add(sizeof(unsigned) * 12);
+    return z.total;
+}
+
+ep_status tan_carve(Arena* ar, int64_t n, int dim, int steps, TanBufs* t, bool rec = true)
+{
+    const size_t m = (size_t)n * dim;
+    EP_TRY(allpairs_carve(ar, (int)n, dim, EP_FP64, &t->ap));
+    if (rec) t->drec = (double*)ar->carve(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));
+    t->dx = (double*)ar->carve(sizeof(double) * 2 * m);
+    t->dacc = (double*)ar->carve(sizeof(double) * 2 * m);
+    t->T[0] = (double*)ar->carve(sizeof(double) * 2 * m);
+    t->T[1] = (double*)ar->carve(sizeof(double) * 2 * m);
+    t->v0 = (double*)ar->carve(sizeof(double) * 2 * m);
+    t->out = (double*)ar->carve(sizeof(double) * 2 * m);
+    t->bar = (unsigned*)ar->carve(sizeof(unsigned) * 12);
+    if (!t->bar) return set_error("workspace too small for the tangent shoot"), EP_ENOMEM;
+    t->err = (int*)(t->bar + 8);
+    return EP_OK;
+}
+
+// Primal shoot from (q0, p0) with every stage input recorded in t.drec.
+ep_status tan_record(const ep_params& P, TanBufs& t, const double* q0, const double* p0, cudaStream_t st)
+{
+    EP_TRY(allpairs_load(P, t.ap, q0, p0, st));
+    return allpairs_steps_rec(P, t.ap, P.steps, P.t1 / P.steps, nullptr, t.drec, st);
+}
+
+template <int DIM, int KER>
+ep_status launch_tangent(TanArgs& a, cudaStream_t st)
+{
+    auto fn = k_tangent_fp64<DIM, KER>;
+    static int resident = -1;
+    if (resident < 0) {
+        int per_sm = 0;
+        EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTanThreads, 0));
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        resident = per_sm * di.sm_count;
+    }
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    const int G = std::max(1, std::min({a.n, di.sm_count, resident}));
+    void* args[] = {&a};
+    count_launch();
+    EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(G), dim3(kTanThreads), args, 0, st));
+    return EP_OK;
+}
+
+// Tangent shoot along t.v0 at the recorded primal trajectory; result in t.out.
+ep_status tan_apply(const ep_params& P, TanBufs& t, int64_t n, cudaStream_t st)
+{
+    TanArgs a{};
+    a.n = (int)n;
+    a.steps = P.steps;
+    a.dt = P.t1 / P.steps;
+    a.sigma = P.sigma;
+    a.drec = t.drec;
+    a.v0 = t.v0;
+    a.dx = t.dx;
+    a.dacc = t.dacc;
+    a.T[0] = t.T[0];
+    a.T[1] = t.T[1];
+    a.out = t.out;
+    a.bar = t.bar;
+    a.err = t.err;
+    EP_TRY_CUDA(cudaMemsetAsync(t.bar, 0, sizeof(unsigned) * 12, st));
+    ep_status s = EP_EINVAL;
+#define EP_TAN_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) s = launch_tangent<D, K>(a, st);
+    EP_TAN_CASE(2, EP_GAUSS) EP_TAN_CASE(2, EP_TENT) EP_TAN_CASE(2, EP_EXPCONE)
+    EP_TAN_CASE(3, EP_GAUSS) EP_TAN_CASE(3, EP_TENT) EP_TAN_CASE(3, EP_EXPCONE)
+#undef EP_TAN_CASE
+    if (s != EP_OK) return s == EP_EINVAL ? (set_error("no tangent kernel for this kernel"), s) : s;
+    int herr = 0;
+    EP_TRY_CUDA(cudaMemcpyAsync(&herr, t.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (herr) return set_error("tangent shoot: a grid-barrier wait gave up (kernel ended early)"), EP_ETIMEOUT;
+    return EP_OK;
+}
+
+bool dev_ptr(const void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+ep_status copy_in(double* dst, const double* src, size_t cnt, cudaStream_t st)
+{
+    EP_TRY_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDefault, st));
+    return EP_OK;
+}
+
+// Restarted GMRES for (D phi) x = b with products y = (D phi) v computed by apply.
+// Stops at |b - (D phi) x| <= tol |b|, after maxit products in total, or at
+// breakdown.  Returns the number of products used.
+template <typename Apply>
+ep_status gmres(Apply apply, const std::vector<double>& b, std::vector<double>& x, int m, int maxit, double tol,
+                int* used)
+{
+    const size_t N = b.size();
+    x.assign(N, 0.0);
+    double bn = 0.0;
+    for (double v : b) bn += v * v;
+    bn = sqrt(bn);
+    *used = 0;
+    if (bn == 0.0) return EP_OK;
+    std::vector<std::vector<double>> V(m + 1, std::vector<double>(N));
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), w(N), y(m);
+    std::vector<double> r(b);
+    bool first = true;
+    while (*used < maxit) {
+        if (!first) {
+            EP_TRY(apply(x, w));
+            ++*used;
+            for (size_t k = 0; k < N; ++k) r[k] = b[k] - w[k];
+        }
+        first = false;
+        double beta = 0.0;
+        for (double v : r) beta += v * v;
+        beta = sqrt(beta);
+        if (beta <= tol * bn) break;
+        for (size_t k = 0; k < N; ++k) V[0][k] = r[k] / beta;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jend = 0;
+        bool converged = false;
+        for (int j = 0; j < m && *used < maxit; ++j) {
+            EP_TRY(apply(V[j], w));
+            ++*used;
+            for (int i = 0; i <= j; ++i) {  // modified Gram-Schmidt
+                double hij = 0.0;
+                for (size_t k = 0; k < N; ++k) hij += w[k] * V[i][k];
+                H[(size_t)i * m + j] = hij;
+                for (size_t k = 0; k < N; ++k) w[k] -= hij * V[i][k];
+            }
+            double hn = 0.0;
+            for (double v : w) hn += v * v;
+            hn = sqrt(hn);
+            H[(size_t)(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {  // previous rotations
+                const double a0 = H[(size_t)i * m + j], a1 = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a0 + sn[i] * a1;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
+            }
+            const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+            const double den = hypot(a0, a1);
+            cs[j] = den > 0.0 ? a0 / den : 1.0;
+            sn[j] = den > 0.0 ? a1 / den : 0.0;
+            H[(size_t)j * m + j] = den;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jend = j + 1;
+            if (fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
+                converged = true;
+                break;
+            }
+            for (size_t k = 0; k < N; ++k) V[j + 1][k] = w[k] / hn;
+        }
+        for (int i = jend - 1; i >= 0; --i) {  // back substitution
+            double s = g[i];
+            for (int k = i + 1; k < jend; ++k) s -= H[(size_t)i * m + k] * y[k];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? s / H[(size_t)i * m + i] : 0.0;
+        }
+        for (int i = 0; i < jend; ++i)
+            for (size_t k = 0; k < N; ++k) x[k] += y[i] * V[i][k];
+        // converged (or broke down) inside the cycle, else restart from the true residual
+        if (jend == 0 || converged) break;
+    }
+    return EP_OK;
+}
+
+}  // namespace
+
+ep_status tangent_entry(const ep_params* params, int64_t n, const double* q0, const double* p0, const double* vq0,
+                        const double* vp0, double* q1, double* p1, double* vq1, double* vp1, void* stream)
+{
+    EP_TRY(check_params(params));
+    const ep_params& P = *params;
+    if (n < 0 || n > ((int64_t)1 << 26)) return set_error("ep_shoot_tangent: bad n"), EP_EINVAL;
+    if (P.precision != EP_FP64) return set_error("ep_shoot_tangent runs in FP64"), EP_EINVAL;
+    if (P.neigh == EP_CELLLIST) return set_error("ep_shoot_tangent runs on the all-pairs path"), EP_EINVAL;
+    if (P.inexact != 0.0) return set_error("ep_shoot_tangent is built for the exact system"), EP_EINVAL;
+    if (n == 0) return EP_OK;
+    if (!q0 || !p0 || !vq0 || !vp0 || !vq1 || !vp1) return set_error("ep_shoot_tangent: NULL array"), EP_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t m = (size_t)n * P.dim;
+    Sizer z;
+    z.add(tan_bytes(n, P.dim, P.steps));
+    z.add(sizeof(double) * m * 2);
+    Arena* ar = nullptr;
+    EP_TRY(arena_acquire(st, z.total, &ar));
+    TanBufs t;
+    EP_TRY(tan_carve(ar, n, P.dim, P.steps, &t));
+    double* dq0 = (double*)ar->carve(sizeof(double) * m);
+    double* dp0 = (double*)ar->carve(sizeof(double) * m);
+    if (!dp0) return set_error("ep_shoot_tangent: workspace too small"), EP_ENOMEM;
+    EP_TRY(copy_in(dq0, q0, m, st));
+    EP_TRY(copy_in(dp0, p0, m, st));
+    EP_TRY(copy_in(t.v0, vq0, m, st));
+    EP_TRY(copy_in(t.v0 + m, vp0, m, st));
+    EP_TRY(tan_record(P, t, dq0, dp0, st));
+    EP_TRY(tan_apply(P, t, n, st));
+    if (q1) EP_TRY_CUDA(cudaMemcpyAsync(q1, t.ap.x, sizeof(double) * m, cudaMemcpyDefault, st));
+    if (p1) EP_TRY_CUDA(cudaMemcpyAsync(p1, t.ap.x + m, sizeof(double) * m, cudaMemcpyDefault, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(vq1, t.out, sizeof(double) * m, cudaMemcpyDefault, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(vp1, t.out + m, sizeof(double) * m, cudaMemcpyDefault, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    return EP_OK;
+}
+
+// Algorithm 1 with a solved gain (Sec. 5): rule EP_RULE_NEWTON takes
+// M = h (D phi)^-1, rule EP_RULE_VELOCITY the paper-literal update of the
+// velocity u = G(X) p with M = h I followed by p = G(X)^-1 u, i.e.
+// p0 += h G(X)^-1 r.  Both solve by restarted GMRES (the Gram matrix of the tent
+// need not be positive definite in two or three dimensions, so no CG).
+ep_status rule_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
+                     ep_match_info* info, cudaStream_t st)
+{
+    const bool newton = info->rule == EP_RULE_NEWTON;
+    const char* name = newton ? "the Newton gain" : "the velocity update";
+    if (P.precision != EP_FP64) return set_error("ep_match: %s runs in FP64", name), EP_EINVAL;
+    if (P.neigh == EP_CELLLIST) return set_error("ep_match: %s runs on the all-pairs path", name), EP_EINVAL;
+    if (P.inexact != 0.0) return set_error("ep_match: %s is built for the exact system", name), EP_EINVAL;
+    if (info->krylov < 0) return set_error("ep_match: krylov must be >= 0"), EP_EINVAL;
+    const size_t m = (size_t)n * P.dim;
+    Sizer z;
+    z.add(tan_bytes(n, P.dim, P.steps, newton));
+    z.add(sizeof(double) * m * 6);
+    Arena* ar = nullptr;
+    EP_TRY(arena_acquire(st, z.total, &ar));
+    TanBufs t;
+    EP_TRY(tan_carve(ar, n, P.dim, P.steps, &t, newton));
+    double* dX = (double*)ar->carve(sizeof(double) * m);
+    double* dp = (double*)ar->carve(sizeof(double) * m);
+    double* dk = (double*)ar->carve(sizeof(double) * m);
+    double* dd = (double*)ar->carve(sizeof(double) * m);
+    double* dv = (double*)ar->carve(sizeof(double) * m);
+    if (!dv) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+    EP_TRY(copy_in(dX, X, m, st));
+    EP_TRY(copy_in(dp, p0, m, st));
+    std::vector<double> hY(m), hp(m), hq(m), r(m), delta;
+    EP_TRY_CUDA(cudaMemcpyAsync(hY.data(), Y, sizeof(double) * m, cudaMemcpyDefault, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(hp.data(), dp, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    const double h = info->h > 0.0 ? info->h : 1.0;
+    info->h = h;
+    const int N = (int)std::min<size_t>(m, (size_t)1 << 30);
+    const int krylov = info->krylov > 0 ? std::min(info->krylov, N) : std::min(N, 200);
+    const int maxprod = 4 * krylov;
+    const bool hist_dev = info->hist && dev_ptr(info->hist);
+    // Newton: (D phi) v, a tangent shoot along (0, v) at the recorded trajectory
+    auto apply_newton = [&](const std::vector<double>& v, std::vector<double>& out) -> ep_status {
+        EP_TRY_CUDA(cudaMemsetAsync(t.v0, 0, sizeof(double) * m, st));
+        EP_TRY_CUDA(cudaMemcpyAsync(t.v0 + m, v.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        EP_TRY(tan_apply(P, t, n, st));
+        EP_TRY_CUDA(cudaMemcpyAsync(out.data(), t.out, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+        return EP_OK;
+    };
+    // velocity rule: G(X) v, the dq of Eq. N-particle at (X, v)
+    auto apply_gram = [&](const std::vector<double>& v, std::vector<double>& out) -> ep_status {
+        EP_TRY_CUDA(cudaMemcpyAsync(dv, v.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        EP_TRY(allpairs_load(P, t.ap, dX, dv, st));
+        EP_TRY(allpairs_rhs(P, t.ap, dk, dd, st));
+        EP_TRY_CUDA(cudaMemcpyAsync(out.data(), dk, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+        return EP_OK;
+    };
+    ep_status status = EP_ENOTCONVERGED;
+    int k = 0;
+    double res = 0.0;
+    for (;;) {
+        // Q(1): the step state x of the all-pairs buffers after the shoot
+        if (newton) {
+            EP_TRY(tan_record(P, t, dX, dp, st));
+        } else {
+            EP_TRY(allpairs_load(P, t.ap, dX, dp, st));
+            EP_TRY(allpairs_steps(P, t.ap, P.steps, P.t1 / P.steps, st));
+        }
+        EP_TRY_CUDA(cudaMemcpyAsync(hq.data(), t.ap.x, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+        res = 0.0;
+        bool finite = true;
+        for (size_t a = 0; a < m; ++a) {
+            r[a] = hY[a] - hq[a];
+            if (!std::isfinite(r[a])) finite = false;
+            res = std::max(res, fabs(r[a]));
+        }
+        if (!finite) res = NAN;
+        if (info->hist) {
+            if (hist_dev)
+                EP_TRY_CUDA(cudaMemcpyAsync(info->hist + k, &res, sizeof(double), cudaMemcpyHostToDevice, st));
+            else
+                info->hist[k] = res;
+        }
+        if (!finite) {
+            status = EP_EDIVERGED;
+            break;
+        }
+        if (res < info->eps) {
+            status = EP_OK;
+            break;
+        }
+        if (k == info->maxit) {
+            status = EP_ENOTCONVERGED;
+            break;
+        }
+        int used = 0;
+        if (newton)
+            EP_TRY(gmres(apply_newton, r, delta, krylov, maxprod, kKrylovTol, &used));
+        else
+            EP_TRY(gmres(apply_gram, r, delta, krylov, maxprod, kKrylovTol, &used));
+        for (size_t a = 0; a < m; ++a) hp[a] += h * delta[a];
+        EP_TRY_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        ++k;
+    }
+    info->iters = k;
+    info->resid_inf = res;
+    EP_TRY_CUDA(cudaMemcpyAsync(p0, dp, sizeof(double) * m, cudaMemcpyDefault, st));
+    // H(X, p0) of Eq. H: 1/2 sum_i p_i . dq_i
+    EP_TRY(allpairs_load(P, t.ap, dX, dp, st));
+    EP_TRY(allpairs_rhs(P, t.ap, dk, dd, st));
+    std::vector<double> hdq(m);
+    EP_TRY_CUDA(cudaMemcpyAsync(hdq.data(), dk, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    double H = 0.0;
+    for (size_t a = 0; a < m; ++a) H += 0.5 * hp[a] * hdq[a];
+    info->H = H;
+    if (status == EP_ENOTCONVERGED) set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", k, res, info->eps);
+    if (status == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", k);
+    return status;
+}
+
+}  // namespace ep

@@ -34,7 +34,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libep.so")
 EXPORTS = ("ep_rhs", "ep_shoot", "ep_match", "ep_adjoint", "ep_match_batched", "ep_hamiltonian",
            "ep_hvp", "ep_cell_neighbors", "ep_release_workspace", "ep_last_error", "ep_version",
            "ep_launch_count", "ep_rhs_noalloc", "ep_set_launch_timing", "ep_last_launch_ms",
-           "ep_last_launch_kernel", "ep_velocity", "ep_flow")
+           "ep_last_launch_kernel", "ep_velocity", "ep_flow", "ep_shoot_tangent")
 
 
 class EPError(RuntimeError):
@@ -52,7 +52,11 @@ class Params(ctypes.Structure):
 class MatchInfo(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("eps", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("iters", ctypes.c_int), ("resid_inf", ctypes.c_double), ("H", ctypes.c_double),
-                ("hist", ctypes.c_void_p)]
+                ("hist", ctypes.c_void_p), ("rule", ctypes.c_int), ("krylov", ctypes.c_int)]
+
+
+# ep_rule: the update of Algorithm 1 step 3 (p0 += h r, h G(X)^-1 r, h (D phi)^-1 r)
+RULE_MOMENTUM, RULE_VELOCITY, RULE_NEWTON = 0, 1, 2
 
 
 @dataclass
@@ -89,6 +93,7 @@ def load():
         "ep_match_batched": [P, ctypes.c_int, VP, VP, VP, VP, ctypes.POINTER(MatchInfo), VP],
         "ep_hamiltonian": [P, I64, VP, VP, VP, VP],
         "ep_hvp": [P, I64, VP, VP, VP, VP, VP, VP, VP],
+        "ep_shoot_tangent": [P, I64, VP, VP, VP, VP, VP, VP, VP, VP, VP],
         "ep_cell_neighbors": [P, I64, VP, VP, VP, VP, VP],
         "ep_release_workspace": [],
         "ep_velocity": [P, I64, VP, VP, I64, VP, VP, VP],
@@ -236,6 +241,19 @@ def shoot(q0, p0, prm: Params):
     return q1, p1
 
 
+def shoot_tangent(q0, p0, vq0, vp0, prm: Params):
+    """ep_shoot_tangent: the RK4 shoot and its derivative along (vq0, vp0) -> (q1, p1, vq1, vp1)."""
+    q0, qp = _prep(q0, "q0")
+    p0, pp = _prep(p0, "p0")
+    vq0, vqp = _prep(vq0, "vq0")
+    vp0, vpp = _prep(vp0, "vp0")
+    n, dim = _shape(q0)
+    q1, p1, vq1, vp1 = (_empty_like(q0) for _ in range(4))
+    _check(load().ep_shoot_tangent(ctypes.byref(_with_dim(prm, dim)), n, qp, pp, vqp, vpp, _ptr(q1), _ptr(p1),
+                                   _ptr(vq1), _ptr(vp1), _stream_for(q0)))
+    return q1, p1, vq1, vp1
+
+
 def velocity(q, p, x, prm: Params):
     """ep_velocity: u(x_k) = sum_j G(|x_k - q_j|) p_j at the points x (Eq. u)."""
     q, qp = _prep(q, "q")
@@ -282,8 +300,10 @@ def _shoots(prm: Params, info: MatchInfo, status: int) -> int:
 
 
 def match(X, Y, prm: Params, h: float = 0.0, eps: float = 1e-6, maxit: int = 200, p0=None,
-          hist: bool = True) -> MatchResult:
-    """ep_match: Algorithm 1 with M = h I on the momenta.  p0=None starts from zero."""
+          hist: bool = True, rule: int = RULE_MOMENTUM, krylov: int = 0) -> MatchResult:
+    """ep_match: Algorithm 1 with the update ``rule`` (RULE_MOMENTUM: M = h I on the
+    momenta; RULE_VELOCITY: p0 += h G(X)^-1 r; RULE_NEWTON: p0 += h (D phi)^-1 r).
+    p0=None starts from zero."""
     X, xp = _prep(X, "X")
     Y, yp = _prep(Y, "Y")
     n, dim = _shape(X)
@@ -301,7 +321,8 @@ def match(X, Y, prm: Params, h: float = 0.0, eps: float = 1e-6, maxit: int = 200
         else:
             p[...] = src
     hbuf = np.full(maxit + 1, np.nan) if hist else None
-    info = MatchInfo(float(h), float(eps), int(maxit), 0, 0.0, 0.0, hbuf.ctypes.data if hist else None)
+    info = MatchInfo(float(h), float(eps), int(maxit), 0, 0.0, 0.0, hbuf.ctypes.data if hist else None,
+                     int(rule), int(krylov))
     st = load().ep_match(ctypes.byref(_with_dim(prm, dim)), n, xp, yp, _ptr(p), ctypes.byref(info),
                          _stream_for(X))
     _check(st, allowed=(OK, ENOTCONVERGED, EDIVERGED))

@@ -1,0 +1,159 @@
+"""The tangent-linear shoot and the solved update rules of Algorithm 1 (Sec. 5: the
+Newton-type gain M = h (D phi)^-1; Algorithm 1 steps 3-4: the velocity update
+p0 += h G(X)^-1 r) on the GPU against the FP64 oracle through the C ABI.
+
+Both sides are FP64; they differ in summation order (the GPU sums a row over CTA
+lanes) and, for the rules, in the linear solve (GPU: restarted GMRES to a 1e-12
+relative residual; oracle: a dense LU).  Uniform clouds of 300 points hold pairs
+a few 1e-3 apart, where the expcone's 1/r and the tangent's 1/r^3 terms amplify the
+rounding of the 300-term sums: the shoot agrees to 1e-11 of its scale and the
+tangent to 1e-10 (the adjoint's bar, which runs through the same Hessian terms);
+converged momenta to 1e-8 of theirs, with equal iteration counts."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as o  # noqa: E402
+from paper_1510_03816_gb300 import ep, workloads as w  # noqa: E402
+
+KSIG = [(ep.GAUSS, 0.2), (ep.TENT, 0.3), (ep.EXPCONE, 0.2)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_03816_gb300 import build
+
+    build.build()
+    o.build()
+    ep.load()
+
+
+def rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def cuda(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def cloud(n, dim, seed, sigma=None, band=1e-9):
+    """Positions in [0.2, 0.8]^dim with no pair distance within band of the tent's kink."""
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        q = rng.uniform(0.2, 0.8, size=(n, dim))
+        if sigma is not None and n > 1:
+            d = np.linalg.norm(q[:, None] - q[None], axis=-1)[np.triu_indices(n, 1)]
+            if np.min(np.abs(d - sigma)) < band:
+                continue
+        return q, rng.normal(0, 0.1, size=(n, dim))
+    raise RuntimeError("no admissible cloud")
+
+
+@pytest.mark.parametrize("kernel,sigma", KSIG)
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("n", [1, 37, 300])
+def test_tangent_shoot_parity(kernel, sigma, dim, n):
+    # 37: fewer particles than CTAs; 300: several rows per CTA (ragged split)
+    q, p = cloud(n, dim, seed=80 + 7 * dim + kernel + n, sigma=sigma if kernel == ep.TENT else None)
+    rng = np.random.default_rng(81 + n)
+    vq, vp = rng.normal(size=q.shape), rng.normal(size=q.shape)
+    steps = 5
+    prm = ep.params(dim=dim, kernel=kernel, sigma=sigma, steps=steps, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    q1, p1, vq1, vp1 = ep.shoot_tangent(cuda(q), cuda(p), cuda(vq), cuda(vp), prm)
+    rq, rp, rvq, rvp = o.shoot_tangent(q, p, vq, vp, kernel, sigma, steps)
+    assert rel(q1, rq) < 1e-11 and rel(p1, rp) < 1e-11
+    assert rel(vq1, rvq) < 1e-10
+    assert rel(vp1, rvp) < 1e-10
+
+
+def test_tangent_shoot_host_arrays_and_linearity():
+    q, p = cloud(64, 2, seed=90)
+    rng = np.random.default_rng(91)
+    v1, v2 = rng.normal(size=q.shape), rng.normal(size=q.shape)
+    z = np.zeros_like(q)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    a = ep.shoot_tangent(q, p, z, v1, prm)[2]
+    b = ep.shoot_tangent(q, p, z, v2, prm)[2]
+    c = ep.shoot_tangent(q, p, z, 2.0 * v1 - 3.0 * v2, prm)[2]
+    assert np.abs(c - (2.0 * a - 3.0 * b)).max() < 1e-12 * np.abs(c).max()
+    assert np.all(ep.shoot_tangent(q, p, z, z, prm)[2] == 0.0)
+
+
+def _match(X, Y, prm, rule, **kw):
+    return ep.match(cuda(X), cuda(Y), prm, rule=rule, **kw)
+
+
+def test_newton_rule_parity():
+    pr = w.circle_to_ellipse(12, sigma=0.1, kernel=ep.GAUSS, steps=10)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(pr.X, pr.Y, prm, ep.RULE_NEWTON, h=1.0, eps=1e-12, maxit=20)
+    rp, st, it, r, hist = o.match_newton(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=1.0, eps=1e-12, maxit=20)
+    assert res.status == st == ep.OK
+    assert res.iters == it
+    assert rel(res.p0, rp) < 1e-8
+    # the residual history agrees while it is far above the solve's accuracy
+    big = hist > 1e-6
+    np.testing.assert_allclose(res.hist[big], hist[big], rtol=1e-6)
+    assert res.H == pytest.approx(o.hamiltonian(pr.X, rp, o.GAUSS, 0.1), rel=1e-9)
+
+
+@pytest.mark.parametrize("kernel,sigma", [(ep.TENT, 0.45), (ep.EXPCONE, 0.3)])
+def test_newton_rule_parity_damped(kernel, sigma):
+    pr = w.circle_to_ellipse(16, sigma=sigma, kernel=kernel, steps=12)
+    prm = ep.params(dim=2, kernel=kernel, sigma=sigma, steps=12, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(pr.X, pr.Y, prm, ep.RULE_NEWTON, h=0.8, eps=1e-10, maxit=40)
+    rp, st, it, r, hist = o.match_newton(pr.X, pr.Y, kernel, sigma, 12, h=0.8, eps=1e-10, maxit=40)
+    assert res.status == st == ep.OK
+    assert abs(res.iters - it) <= 1
+    assert rel(res.p0, rp) < 1e-7
+
+
+@pytest.mark.parametrize("kernel,sigma,h", [(ep.TENT, 0.45, 0.5), (ep.EXPCONE, 0.3, 0.7), (ep.GAUSS, 0.12, 0.6)])
+def test_velocity_rule_parity(kernel, sigma, h):
+    pr = w.circle_to_ellipse(16, sigma=sigma, kernel=kernel, steps=20)
+    prm = ep.params(dim=2, kernel=kernel, sigma=sigma, steps=20, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(pr.X, pr.Y, prm, ep.RULE_VELOCITY, h=h, eps=1e-8, maxit=100)
+    rp, st, it, r, hist = o.match_velocity(pr.X, pr.Y, kernel, sigma, 20, h=h, eps=1e-8, maxit=100)
+    assert res.status == st
+    assert abs(res.iters - it) <= 1
+    k = min(len(res.hist), len(hist))
+    np.testing.assert_allclose(res.hist[:k], hist[:k], rtol=1e-6, atol=1e-12)
+    if res.iters == it:
+        assert rel(res.p0, rp) < 1e-8
+
+
+def test_velocity_rule_fixed_iterations_3d():
+    # a fixed number of updates compared iterate by iterate (no convergence test involved)
+    X, p = cloud(40, 3, seed=95)
+    Y = X + 0.05 * np.random.default_rng(96).normal(size=X.shape)
+    prm = ep.params(dim=3, kernel=ep.EXPCONE, sigma=0.15, steps=8, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_VELOCITY, h=0.5, eps=0.0, maxit=6)
+    rp, st, it, r, hist = o.match_velocity(X, Y, ep.EXPCONE, 0.15, 8, h=0.5, eps=0.0, maxit=6)
+    assert res.status == st == ep.ENOTCONVERGED and res.iters == it == 6
+    assert rel(res.p0, rp) < 1e-9
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-9)
+
+
+def test_rule_refusals():
+    X, _ = cloud(20, 2, seed=97)
+    Y = X + 0.01
+    for prec in (ep.MIXED,):
+        prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=prec, neigh=ep.ALLPAIRS)
+        for rule in (ep.RULE_NEWTON, ep.RULE_VELOCITY):
+            with pytest.raises(ep.EPError):
+                _match(X, Y, prm, rule, maxit=3)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS, inexact=0.1)
+    with pytest.raises(ep.EPError):
+        _match(X, Y, prm, ep.RULE_NEWTON, maxit=3)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    with pytest.raises(ep.EPError):
+        _match(X, Y, prm, 7, maxit=3)
+    with pytest.raises(ep.EPError):
+        ep.shoot_tangent(X, X, X, X, ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.MIXED,
+                                               neigh=ep.ALLPAIRS))
