@@ -50,6 +50,9 @@ FLOPS_PER_PAIR_2D_GAUSS = 19  # algorithmic flops of one (i, j) term of Eq. N-pa
 FLOPS_PER_PAIR_2D_TENT = 20   # accepted tent pair: d, r^2, rsqrt, G, dq, p_i.p_j, weight, dp
 FLOPS_PER_PAIR_3D_GAUSS = 28  # d (3), r^2 (5), G (2), dq (6), p_i.p_j (5), weight (1), dp (6)
 FLOPS_PER_PAIR_3D_HVP = 65    # one (i, j) term of the Hessian-vector product of H (both blocks)
+FLOPS_PER_PAIR_2D_TANGENT = 58  # FP64 tangent pair: d, dd (4), r^2, d.dd, p.p (12), dp.p + p.dp (8),
+                                # phi, psi (6), dq block (10), dp block (18); exp not counted
+FP64_LANES_PER_SM = 2  # FP64 FMA per clock per SM (one warp instruction per 64 cycles per SMSP)
 WORKLOAD = ("fourier_curve_warp: N=4096 2-D landmarks on a random Fourier curve -> sine warp; "
             "Gaussian sigma=0.1; RK4 100 steps on [0,1]; Algorithm 1 from p0=0, eps=1e-6 (max-norm), maxit=200; "
             "default gain h = 1/max_i sum_j G_ij")
@@ -290,6 +293,10 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def dev_sm_count(torch) -> int:
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def _events_ms(torch, stream, fn, reps):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fn()
@@ -437,8 +444,8 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
         out[f"small_{name}"] = {"workload": "circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, maxit 200",
                                 "seconds_per_match": dt, "iters": r.iters, "resid": r.resid,
                                 "shoots_per_s": (r.iters + 1) / dt,
-                                "roofline": {"bound": "latency", "note": "one CTA, 200 dependent shoots of 200 "
-                                             "dependent RHS; reported as shoots/s"}}
+                                "roofline": {"bound": "latency", "note": "one launch: 201 dependent shoots of 200 dependent "
+                                             "RHS (FP64: cooperative, 64 CTAs; mixed: one CTA); reported as shoots/s"}}
     # the inexact system (Sec. 6): circle -> ellipse, sigma_n^2 = 0.05, FP64, momentum-difference stop
     prmi = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.FP64, neigh=ep.ALLPAIRS,
                      inexact=0.05)
@@ -450,6 +457,66 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
                            "seconds_per_match": dt, "iters": r.iters, "status": r.status, "resid": r.resid,
                            "shoots_per_s": r.iters / dt,
                            "roofline": {"bound": "latency", "note": "one cooperative launch, FP64 pairs on 64 SMs"}}
+    # the tangent-linear shoot (Sec. 5, D phi along one direction): N=1024 Fourier curve, FP64
+    fcs = workloads.fourier_curve_warp(n=1024, steps=50)
+    Xt = torch.tensor(fcs.X, device=dev)
+    pt = torch.tensor(0.002 * (fcs.Y - fcs.X), device=dev)
+    vt = torch.tensor(np.random.default_rng(3).normal(size=fcs.X.shape), device=dev)
+    zt = torch.zeros_like(Xt)
+    prmt = ep.params(dim=2, kernel=fcs.kernel, sigma=fcs.sigma, steps=fcs.steps, precision=ep.FP64,
+                     neigh=ep.ALLPAIRS)
+    ms, _ = _events_ms(torch, stream, lambda: ep.shoot_tangent(Xt, pt, zt, vt, prmt), 3)
+    ep.set_launch_timing(True)
+    ep.shoot_tangent(Xt, pt, zt, vt, prmt)
+    lt_ms, lt_name = ep.last_launch()
+    ep.set_launch_timing(False)
+    tpairs = fcs.n ** 2 * 4 * fcs.steps
+    fp64_peak = dev_sm_count(torch) * FP64_LANES_PER_SM * 2 * 2070e6 / 1e12
+    out["tangent_fp64"] = {"workload": "fourier_curve_warp N=1024, Gaussian sigma=0.1, 50 steps, FP64: recorded "
+                                       "primal shoot + tangent shoot along (0, v)",
+                           "ms_per_call": ms, "tangent_kernel": lt_name, "tangent_launch_ms": lt_ms,
+                           "pair_interactions_per_s": tpairs / (lt_ms * 1e-3),
+                           "roofline": dict(_alu_roofline(tpairs * FLOPS_PER_PAIR_2D_TANGENT / (lt_ms * 1e-3),
+                                                          fp64_peak,
+                                                          f"FP64: {FLOPS_PER_PAIR_2D_TANGENT} flop per tangent pair "
+                                                          f"(exp not counted) against {FP64_LANES_PER_SM} DFMA per "
+                                                          "clock per SM at 2070 MHz"),
+                                            unit="TFLOP/s (FP64)")}
+    if with_cpu:
+        sub = fcs.X[::4], 0.002 * (fcs.Y - fcs.X)[::4]
+        k = (fcs.n / sub[0].shape[0]) ** 2 * (fcs.steps / 5)
+        out["tangent_fp64"]["cpu_baseline"] = _oracle_sample(
+            lambda o: (o.shoot_tangent(sub[0], sub[1], np.zeros_like(sub[0]), np.ones_like(sub[0]), fcs.kernel,
+                                       fcs.sigma, 5), fcs.n ** 2 * 4 * fcs.steps / k)[1],
+            UNIT, f"FP64 oracle tangent shoot (primal + tangent) at N={sub[0].shape[0]}, 5 steps; tangent pairs "
+                  "counted as on the GPU")
+    # the solved update rules on the N = 64 circle -> ellipse (tent sigma = 0.25, 50 steps, target noise),
+    # where the momentum rule stays above 1e-6 after 200 iterations
+    for name, rule, h in (("newton_fp64", ep.RULE_NEWTON, 1.0), ("velocity_fp64", ep.RULE_VELOCITY, 0.5)):
+        prmc = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.FP64, neigh=ep.ALLPAIRS)
+        ep.match(Xc, Yc, prmc, h=h, eps=c.eps, maxit=c.maxit, rule=rule)
+        t0 = time.perf_counter()
+        r = ep.match(Xc, Yc, prmc, h=h, eps=c.eps, maxit=c.maxit, rule=rule)
+        dt = time.perf_counter() - t0
+        note = (f"host GMRES; each of the {r.products} tangent shoots is one cooperative launch of 200 "
+                "dependent FP64 stages on 64 particles" if rule == ep.RULE_NEWTON else
+                f"one cooperative launch: 43 shoots of 200 dependent FP64 stages and {r.products} MINRES "
+                "iterations (stored G(X) product, two grid sums, three grid barriers each)")
+        out[name] = {"workload": f"circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, FP64, h={h}, "
+                                 + ("Newton gain h (D phi)^-1" if rule == ep.RULE_NEWTON else "velocity update "
+                                    "h G(X)^-1 r"),
+                     "seconds_per_match": dt, "matchings_per_s": 1.0 / dt, "iters": r.iters, "status": r.status,
+                     "resid": r.resid, "krylov_products": r.products,
+                     "roofline": {"bound": "latency", "note": note}}
+        if with_cpu:
+            fn = "match_newton" if rule == ep.RULE_NEWTON else "match_velocity"
+
+            def run_rule(o, fn=fn, h=h):
+                getattr(o, fn)(c.X, c.Y, c.kernel, c.sigma, c.steps, h=h, eps=c.eps, maxit=c.maxit)
+                return 1.0
+
+            out[name]["cpu_baseline"] = _oracle_sample(
+                run_rule, "matchings/s", f"FP64 oracle {fn} (dense Jacobian or Gram matrix, LU solve), whole match")
     if with_cpu:
         def run_small(o):
             _, _, it, _, _ = o.match(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.0, eps=c.eps, maxit=c.maxit)

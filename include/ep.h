@@ -61,9 +61,12 @@ typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
  *                                              from u (Algorithm 1 step 4)
  *  EP_RULE_NEWTON    p0 += h (D phi)^-1 r      the gain M = h (D phi)^-1 of Theorem 1,
  *                                              D phi = dQ(1)/dp0 of the RK4 shoot
- * The two solved rules run restarted GMRES (ep_match_info.krylov vectors) whose
- * products are the all-pairs Gram product G(X) v (velocity) or a tangent-linear
- * shoot along (0, v) (Newton); they are FP64, all-pairs, exact system only. */
+ * Both solved rules are FP64, all-pairs, exact system only (EP_EINVAL otherwise).
+ * The velocity rule runs inside the device-resident matching launch: MINRES on the
+ * symmetric G(X) (the tent's need not be positive definite), one all-pairs Gram
+ * product per iteration.  The Newton rule runs restarted GMRES on the host
+ * (ep_match_info.krylov vectors) whose products are tangent-linear shoots along
+ * (0, v) on the device (ep_shoot_tangent). */
 typedef enum { EP_RULE_MOMENTUM = 0, EP_RULE_VELOCITY = 1, EP_RULE_NEWTON = 2 } ep_rule;
 
 typedef struct {
@@ -96,9 +99,11 @@ typedef struct {
                         residual of every shoot; NULL for none */
     int rule;        /* in: ep_rule (0 = EP_RULE_MOMENTUM).  For the solved rules h <= 0
                         means h = 1; ep_match_batched requires EP_RULE_MOMENTUM */
-    int krylov;      /* in: GMRES restart length of the solved rules (0 = min(n dim, 200));
-                        the inner solve stops at relative residual 1e-12 or after 4 krylov
-                        products */
+    int krylov;      /* in: Krylov size of the solved rules (0 = min(n dim, 200)): the GMRES
+                        restart length (Newton); the inner solve (GMRES or MINRES) stops at
+                        relative residual 1e-12 or after 4 krylov products */
+    int products;    /* out: matrix-vector products of the solved rules (tangent shoots or
+                        Gram products) over the whole matching; 0 for the momentum rule */
 } ep_match_info;
 
 /* Right-hand side of the N-particle system (Sec. 3.1, Eq. N-particle):

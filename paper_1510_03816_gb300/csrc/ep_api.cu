@@ -506,12 +506,21 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     info->iters = 0;
     info->resid_inf = 0.0;
     info->H = 0.0;
+    info->products = 0;
     if (n == 0) {
         if (info->h <= 0.0) info->h = 1.0;
         return EP_OK;
     }
-    // the solved update rules (velocity, Newton): host GMRES over device products
-    if (info->rule != EP_RULE_MOMENTUM) return rule_match(P, n, X, Y, p0, info, st);
+    // the plain FP64 all-pairs method runs the whole feedback loop on the device, with
+    // the momentum rule or the velocity rule (in-kernel MINRES)
+    const bool device_loop = P.precision == EP_FP64 && !use_celllist(P, n) &&
+                             ((info->rule == EP_RULE_MOMENTUM && n <= kDeviceMatchMaxN) ||
+                              (info->rule == EP_RULE_VELOCITY && P.inexact == 0.0));
+    if (info->rule == EP_RULE_VELOCITY && !device_loop)
+        return set_error("ep_match: the velocity update runs in FP64 on the all-pairs path of the exact system"),
+               EP_EINVAL;
+    // the Newton gain: host GMRES over tangent-linear shoots on the device
+    if (info->rule == EP_RULE_NEWTON) return rule_match(P, n, X, Y, p0, info, st);
     // small 2-D mixed problems: the whole feedback loop on one CTA (no grid-wide sync per stage)
     if (P.precision == EP_MIXED && P.dim == 2 && !use_celllist(P, n) && n <= kSmallMatchMaxN && P.inexact == 0.0) {
         ep_status s = match_small(params, n, X, Y, p0, info, stream);
@@ -521,11 +530,9 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         return s;
     }
     const bool hist_dev = info->hist && is_device_ptr(info->hist);
-    // the plain FP64 all-pairs method: the whole feedback loop on the device
-    const bool device_loop = P.precision == EP_FP64 && !use_celllist(P, n) && n <= kDeviceMatchMaxN;
     Sizer z;
     if (device_loop) {
-        z.add(match_device_bytes(n, P.dim, info->maxit));
+        z.add(match_device_bytes(n, P.dim, info->maxit, info->rule));
         z.add(sizeof(double) * ((size_t)info->maxit + 1));
     }
     z.add(forward_bytes(P, n));
@@ -545,8 +552,9 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     if (device_loop) {
         double* hist_d = hist_dev ? info->hist : nullptr;
         if (info->hist && !hist_dev) hist_d = (double*)ar->carve(sizeof(double) * ((size_t)info->maxit + 1));
-        double out[5];
+        double out[6];
         EP_TRY(match_device_fp64(P, n, sX.dev, sY.dev, sp.dev, info, hist_d, ar, st, out));
+        info->products = (int)out[5];
         info->h = out[0];
         info->resid_inf = out[1];
         info->H = out[2];

@@ -42,10 +42,11 @@ ep_status match_small(const ep_params* params, int64_t n, const double* X, const
 // Algorithm 1 for the plain FP64 method in one cooperative launch (ep_match_dev.cu):
 // X, Y, p0 device arrays (p0 in/out), hist_dev maxit + 1 doubles on the device or
 // null; workspace from ar (match_device_bytes); out = h, residual, H, iterations,
-// status.
-size_t match_device_bytes(int64_t n, int dim, int maxit);
+// status, Gram products (the velocity rule's MINRES iterations).  Runs the momentum
+// rule and the velocity rule (info->rule).
+size_t match_device_bytes(int64_t n, int dim, int maxit, int rule);
 ep_status match_device_fp64(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
-                            ep_match_info* info, double* hist_dev, Arena* ar, cudaStream_t st, double out[5]);
+                            ep_match_info* info, double* hist_dev, Arena* ar, cudaStream_t st, double out[6]);
 constexpr int64_t kDeviceMatchMaxN = 16384;
 
 // Tangent-linear shoot and the solved update rules of ep_match (ep_newton.cu).

@@ -29,6 +29,7 @@
 #include <cmath>
 #include <vector>
 
+#include "ep_allpairs.cuh"
 #include "ep_allpairs_dev.cuh"
 #include "ep_features.cuh"
 
@@ -210,23 +211,23 @@ struct TanBufs {
     int* err = nullptr;
 };
 
-size_t tan_bytes(int64_t n, int dim, int steps, bool rec = true)
+size_t tan_bytes(int64_t n, int dim, int steps)
 {
     Sizer z;
     const size_t m = (size_t)n * dim;
     z.add(allpairs_bytes((int)n, dim, EP_FP64));
-    if (rec) z.add(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));  // recorded stages
+    z.add(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));  // recorded stages
     for (int k = 0; k < 4; ++k) z.add(sizeof(double) * 2 * m);  // dx, dacc, T[2]
     z.add(sizeof(double) * 2 * m * 2);                          // v0, out
     z.add(sizeof(unsigned) * 12);
     return z.total;
 }
 
-ep_status tan_carve(Arena* ar, int64_t n, int dim, int steps, TanBufs* t, bool rec = true)
+ep_status tan_carve(Arena* ar, int64_t n, int dim, int steps, TanBufs* t)
 {
     const size_t m = (size_t)n * dim;
     EP_TRY(allpairs_carve(ar, (int)n, dim, EP_FP64, &t->ap));
-    if (rec) t->drec = (double*)ar->carve(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));
+    t->drec = (double*)ar->carve(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));
     t->dx = (double*)ar->carve(sizeof(double) * 2 * m);
     t->dacc = (double*)ar->carve(sizeof(double) * 2 * m);
     t->T[0] = (double*)ar->carve(sizeof(double) * 2 * m);
@@ -285,16 +286,30 @@ ep_status tan_apply(const ep_params& P, TanBufs& t, int64_t n, cudaStream_t st)
     a.bar = t.bar;
     a.err = t.err;
     EP_TRY_CUDA(cudaMemsetAsync(t.bar, 0, sizeof(unsigned) * 12, st));
+    // optional CUDA events around the launch (ep_set_launch_timing)
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (launch_timing_enabled() && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+        if (e0) cudaEventDestroy(e0);
+        e0 = e1 = nullptr;
+    }
+    if (e0) cudaEventRecord(e0, st);
     ep_status s = EP_EINVAL;
 #define EP_TAN_CASE(D, K) \
     if (P.dim == D && P.kernel == K) s = launch_tangent<D, K>(a, st);
     EP_TAN_CASE(2, EP_GAUSS) EP_TAN_CASE(2, EP_TENT) EP_TAN_CASE(2, EP_EXPCONE)
     EP_TAN_CASE(3, EP_GAUSS) EP_TAN_CASE(3, EP_TENT) EP_TAN_CASE(3, EP_EXPCONE)
 #undef EP_TAN_CASE
-    if (s != EP_OK) return s == EP_EINVAL ? (set_error("no tangent kernel for this kernel"), s) : s;
+    if (e0) cudaEventRecord(e1, st);
     int herr = 0;
-    EP_TRY_CUDA(cudaMemcpyAsync(&herr, t.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (s == EP_OK) s = cudaMemcpyAsync(&herr, t.err, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess
+                            ? EP_OK : cuda_fail(cudaGetLastError(), "tangent error flag");
+    if (s == EP_OK) s = cudaStreamSynchronize(st) == cudaSuccess ? EP_OK : cuda_fail(cudaGetLastError(), "tangent sync");
+    if (e0 && s == EP_OK) record_launch_time(e0, e1, "k_tangent_fp64");
+    if (e0) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (s != EP_OK) return s == EP_EINVAL ? (set_error("no tangent kernel for this kernel"), s) : s;
     if (herr) return set_error("tangent shoot: a grid-barrier wait gave up (kernel ended early)"), EP_ETIMEOUT;
     return EP_OK;
 }
@@ -434,34 +449,29 @@ ep_status tangent_entry(const ep_params* params, int64_t n, const double* q0, co
     return EP_OK;
 }
 
-// Algorithm 1 with a solved gain (Sec. 5): rule EP_RULE_NEWTON takes
-// M = h (D phi)^-1, rule EP_RULE_VELOCITY the paper-literal update of the
-// velocity u = G(X) p with M = h I followed by p = G(X)^-1 u, i.e.
-// p0 += h G(X)^-1 r.  Both solve by restarted GMRES (the Gram matrix of the tent
-// need not be positive definite in two or three dimensions, so no CG).
+// Algorithm 1 with the Newton-type gain M = h (D phi)^-1 of Sec. 5 (Theorem 1):
+// (D phi) delta = r solved by restarted GMRES (D phi is not symmetric) whose
+// products are tangent shoots.
 ep_status rule_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
                      ep_match_info* info, cudaStream_t st)
 {
-    const bool newton = info->rule == EP_RULE_NEWTON;
-    const char* name = newton ? "the Newton gain" : "the velocity update";
-    if (P.precision != EP_FP64) return set_error("ep_match: %s runs in FP64", name), EP_EINVAL;
-    if (P.neigh == EP_CELLLIST) return set_error("ep_match: %s runs on the all-pairs path", name), EP_EINVAL;
-    if (P.inexact != 0.0) return set_error("ep_match: %s is built for the exact system", name), EP_EINVAL;
+    if (P.precision != EP_FP64) return set_error("ep_match: the Newton gain runs in FP64"), EP_EINVAL;
+    if (P.neigh == EP_CELLLIST) return set_error("ep_match: the Newton gain runs on the all-pairs path"), EP_EINVAL;
+    if (P.inexact != 0.0) return set_error("ep_match: the Newton gain is built for the exact system"), EP_EINVAL;
     if (info->krylov < 0) return set_error("ep_match: krylov must be >= 0"), EP_EINVAL;
     const size_t m = (size_t)n * P.dim;
     Sizer z;
-    z.add(tan_bytes(n, P.dim, P.steps, newton));
+    z.add(tan_bytes(n, P.dim, P.steps));
     z.add(sizeof(double) * m * 6);
     Arena* ar = nullptr;
     EP_TRY(arena_acquire(st, z.total, &ar));
     TanBufs t;
-    EP_TRY(tan_carve(ar, n, P.dim, P.steps, &t, newton));
+    EP_TRY(tan_carve(ar, n, P.dim, P.steps, &t));
     double* dX = (double*)ar->carve(sizeof(double) * m);
     double* dp = (double*)ar->carve(sizeof(double) * m);
     double* dk = (double*)ar->carve(sizeof(double) * m);
     double* dd = (double*)ar->carve(sizeof(double) * m);
-    double* dv = (double*)ar->carve(sizeof(double) * m);
-    if (!dv) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+    if (!dd) return set_error("ep_match: workspace too small"), EP_ENOMEM;
     EP_TRY(copy_in(dX, X, m, st));
     EP_TRY(copy_in(dp, p0, m, st));
     std::vector<double> hY(m), hp(m), hq(m), r(m), delta;
@@ -474,8 +484,8 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     const int krylov = info->krylov > 0 ? std::min(info->krylov, N) : std::min(N, 200);
     const int maxprod = 4 * krylov;
     const bool hist_dev = info->hist && dev_ptr(info->hist);
-    // Newton: (D phi) v, a tangent shoot along (0, v) at the recorded trajectory
-    auto apply_newton = [&](const std::vector<double>& v, std::vector<double>& out) -> ep_status {
+    // (D phi) v: a tangent shoot along (0, v) at the recorded trajectory
+    auto apply = [&](const std::vector<double>& v, std::vector<double>& out) -> ep_status {
         EP_TRY_CUDA(cudaMemsetAsync(t.v0, 0, sizeof(double) * m, st));
         EP_TRY_CUDA(cudaMemcpyAsync(t.v0 + m, v.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
         EP_TRY(tan_apply(P, t, n, st));
@@ -483,26 +493,12 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
         EP_TRY_CUDA(cudaStreamSynchronize(st));
         return EP_OK;
     };
-    // velocity rule: G(X) v, the dq of Eq. N-particle at (X, v)
-    auto apply_gram = [&](const std::vector<double>& v, std::vector<double>& out) -> ep_status {
-        EP_TRY_CUDA(cudaMemcpyAsync(dv, v.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-        EP_TRY(allpairs_load(P, t.ap, dX, dv, st));
-        EP_TRY(allpairs_rhs(P, t.ap, dk, dd, st));
-        EP_TRY_CUDA(cudaMemcpyAsync(out.data(), dk, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-        EP_TRY_CUDA(cudaStreamSynchronize(st));
-        return EP_OK;
-    };
     ep_status status = EP_ENOTCONVERGED;
     int k = 0;
     double res = 0.0;
     for (;;) {
-        // Q(1): the step state x of the all-pairs buffers after the shoot
-        if (newton) {
-            EP_TRY(tan_record(P, t, dX, dp, st));
-        } else {
-            EP_TRY(allpairs_load(P, t.ap, dX, dp, st));
-            EP_TRY(allpairs_steps(P, t.ap, P.steps, P.t1 / P.steps, st));
-        }
+        // Q(1): the step state x of the all-pairs buffers after the recorded shoot
+        EP_TRY(tan_record(P, t, dX, dp, st));
         EP_TRY_CUDA(cudaMemcpyAsync(hq.data(), t.ap.x, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
         EP_TRY_CUDA(cudaStreamSynchronize(st));
         res = 0.0;
@@ -532,10 +528,8 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
             break;
         }
         int used = 0;
-        if (newton)
-            EP_TRY(gmres(apply_newton, r, delta, krylov, maxprod, kKrylovTol, &used));
-        else
-            EP_TRY(gmres(apply_gram, r, delta, krylov, maxprod, kKrylovTol, &used));
+        EP_TRY(gmres(apply, r, delta, krylov, maxprod, kKrylovTol, &used));
+        info->products += used;
         for (size_t a = 0; a < m; ++a) hp[a] += h * delta[a];
         EP_TRY_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
         ++k;

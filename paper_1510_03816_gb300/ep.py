@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
 class MatchInfo(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("eps", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("iters", ctypes.c_int), ("resid_inf", ctypes.c_double), ("H", ctypes.c_double),
-                ("hist", ctypes.c_void_p), ("rule", ctypes.c_int), ("krylov", ctypes.c_int)]
+                ("hist", ctypes.c_void_p), ("rule", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("products", ctypes.c_int)]
 
 
 # ep_rule: the update of Algorithm 1 step 3 (p0 += h r, h G(X)^-1 r, h (D phi)^-1 r)
@@ -68,6 +69,7 @@ class MatchResult:
     H: float
     h: float
     hist: object | None
+    products: int = 0
 
 
 _lib = None
@@ -327,7 +329,7 @@ def match(X, Y, prm: Params, h: float = 0.0, eps: float = 1e-6, maxit: int = 200
                          _stream_for(X))
     _check(st, allowed=(OK, ENOTCONVERGED, EDIVERGED))
     return MatchResult(p, st, info.iters, info.resid_inf, info.H, info.h,
-                       hbuf[: _shoots(prm, info, st)] if hist else None)
+                       hbuf[: _shoots(prm, info, st)] if hist else None, info.products)
 
 
 def hvp(q, p, vq, vp, prm: Params):

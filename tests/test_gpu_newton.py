@@ -138,6 +138,20 @@ def test_velocity_rule_fixed_iterations_3d():
     assert res.status == st == ep.ENOTCONVERGED and res.iters == it == 6
     assert rel(res.p0, rp) < 1e-9
     np.testing.assert_allclose(res.hist, hist, rtol=1e-9)
+    assert res.products >= 6
+
+
+def test_velocity_rule_ragged_rows_2d():
+    # 300 landmarks: two rows on most CTAs, one on the rest (the MINRES sums span every CTA)
+    # (tent sigma = 0.03 against a mean spacing of 0.035: cond G(X) = 31)
+    X, _ = cloud(300, 2, seed=98, sigma=0.03)
+    Y = X + 0.005 * np.random.default_rng(99).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=0.03, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_VELOCITY, h=0.5, eps=0.0, maxit=3)
+    rp, st, it, r, hist = o.match_velocity(X, Y, ep.TENT, 0.03, 4, h=0.5, eps=0.0, maxit=3)
+    assert res.iters == it == 3
+    assert rel(res.p0, rp) < 1e-9
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-9)
 
 
 def test_rule_refusals():
