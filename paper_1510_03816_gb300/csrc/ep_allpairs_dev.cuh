@@ -230,6 +230,56 @@ __device__ void epilogue_mixed(const StageArgs& a, int i)
     epilogue_mixed_k<DIM>(a, i, kk);
 }
 
+// Sum of V <= 8 doubles over a CTA of THREADS threads, complete in every thread on
+// return; sm holds (THREADS / 32 + 1) * 8 doubles.  An FP64 warp instruction holds
+// its sub-partition's FP64 pipe for the same time whatever the number of active
+// lanes, so the sum minimises FP64 instructions: a reduce-scatter butterfly over
+// the lanes (each round halves the values a lane holds: 6 adds for 4 values, 9 for
+// 8, against 5 per value for a plain butterfly), then one thread per value adds
+// the warps' totals.  Fixed order: the same bits on every call and in every CTA.
+template <int V, int THREADS>
+__device__ __forceinline__ void cta_sum_f64(double (&v)[V], double* sm)
+{
+    static_assert(V >= 1 && V <= 8, "cta_sum_f64 takes 1 to 8 values");
+    constexpr int W = THREADS / 32;
+    constexpr int P = V == 1 ? 1 : V == 2 ? 2 : V <= 4 ? 4 : 8;  // padded to a power of two
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double u[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) u[k] = k < V ? v[k] : 0.0;
+    int first = 0;  // the value index this lane ends up holding
+    int cnt = P;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (cnt > 1) {
+            const int h = cnt / 2;
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < P / 2; ++k) {
+                if (k < h) {
+                    const double send = upper ? u[k] : u[k + h];
+                    const double keep = upper ? u[k + h] : u[k];
+                    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            if (upper) first += h;
+            cnt = h;
+        } else {
+            u[0] += __shfl_xor_sync(0xffffffffu, u[0], o);
+        }
+    }
+    if ((lane & (32 / P - 1)) == 0 && first < V) sm[warp * P + first] = u[0];
+    __syncthreads();
+    if (threadIdx.x < V) {
+        double t = 0.0;
+        for (int w = 0; w < W; ++w) t += sm[w * P + threadIdx.x];
+        sm[W * P + threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < V; ++k) v[k] = sm[W * P + k];
+}
+
 // Grid-wide barrier of a cooperative launch (all CTAs resident).  The counter
 // only grows: barrier number e completes when it reaches e * gridDim.x.  The
 // wait is bounded; on giving up it raises the shared error flag, and every CTA

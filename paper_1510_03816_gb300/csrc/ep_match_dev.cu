@@ -77,27 +77,10 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// Sum of V doubles over the CTA; the result is valid in every thread.
 template <int V>
 __device__ __forceinline__ void cta_sum(double (&v)[V], double* sm)
 {
-    constexpr int W = kMatchThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < V; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < V; ++k) sm[warp * V + k] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        double s = 0.0;
-        for (int w = 0; w < W; ++w) s += sm[w * V + k];
-        v[k] = s;
-    }
+    cta_sum_f64<V, kMatchThreads>(v, sm);
 }
 
 __device__ __forceinline__ unsigned long long cta_max_bits(unsigned long long v, unsigned long long* sm)
@@ -318,7 +301,7 @@ template <int DIM, int KER>
 __global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
 {
     constexpr int S2 = 2 * DIM;
-    __shared__ double sm_d[(kMatchThreads / 32) * S2];
+    __shared__ double sm_d[(kMatchThreads / 32 + 1) * 8];
     __shared__ unsigned long long sm_u[kMatchThreads / 32];
     const int n = a.n;
     const int r0 = (int)((long long)blockIdx.x * n / gridDim.x), r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);

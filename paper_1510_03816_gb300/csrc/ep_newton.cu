@@ -81,34 +81,11 @@ struct TanArgs {
     int* err;
 };
 
-// Sum of V doubles over the CTA; complete in every thread.
-template <int V>
-__device__ __forceinline__ void tan_cta_sum(double (&v)[V], double* sm)
-{
-    constexpr int W = kTanThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < V; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < V; ++k) sm[warp * V + k] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        double s = 0.0;
-        for (int w = 0; w < W; ++w) s += sm[w * V + k];
-        v[k] = s;
-    }
-}
-
 template <int DIM, int KER>
 __global__ void __launch_bounds__(kTanThreads) k_tangent_fp64(TanArgs a)
 {
     constexpr int S2 = 2 * DIM;
-    __shared__ double sm_d[(kTanThreads / 32) * S2];
+    __shared__ double sm_d[(kTanThreads / 32 + 1) * 8];
     const int n = a.n;
     const int r0 = (int)((long long)blockIdx.x * n / gridDim.x), r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
     const size_t nd = (size_t)n * DIM;
@@ -163,7 +140,7 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_fp64(TanArgs a)
                         for (int c = 0; c < DIM; ++c) h[DIM + c] += a1 * phi * d[c] + pp * (phi * dv[c] + psi * ddv * d[c]);
                     }
                 }
-                tan_cta_sum<S2>(h, sm_d);
+                cta_sum_f64<S2, kTanThreads>(h, sm_d);
                 // dk = (h_p, -h_q); the tangent RK4 stage, one thread per component
                 if (threadIdx.x < S2) {
                     const int c = threadIdx.x;
