@@ -27,6 +27,7 @@
 // anchor + c dt k in FP32 on the offsets (re-celled by floor(o / e)); the step
 // state x is FP64 and the anchor is re-derived from it in FP64 every step.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -69,7 +70,7 @@ struct Impl {
     int* count[2];   // per cell (ping-pong by stage), then local exclusive scan
     int* bsum;       // per scan block total, then exclusive block offsets
     int* scan_ctr;   // arrival counter of the block scan
-    double* bbox;    // min x, min y, max x, max y
+    double* bbox;    // keys (k_bbox2) of min x, min y, max x, max y
     Grid g;
     int cur;         // count buffer holding the next stage's bins
 };
@@ -127,28 +128,56 @@ __device__ __forceinline__ void locate(double q, int axis, const Grid& g, int& c
 }
 
 // ------------------------------------------------------------------ kernels
-__global__ void k_bbox2(const double* __restrict__ q, int n, double* out)
+// Order-preserving map of a double to an unsigned key (negative values flipped
+// whole, non-negative ones get the sign bit), so min / max become integer atomics.
+__device__ __forceinline__ unsigned long long dkey(double v)
 {
-    __shared__ double s[4][32];
-    double v[4] = {INFINITY, INFINITY, -INFINITY, -INFINITY};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+inline double dkey_value(unsigned long long k)
+{
+    const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    double v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+// Bounding box of the n positions q (2-D), NaN coordinates ignored: each CTA
+// reduces a grid-strided share and merges it into out[0..3] (keys of min x, min y,
+// max x, max y; initialised to the identities) by integer atomics.
+__global__ void __launch_bounds__(256) k_bbox2(const double* __restrict__ q, int n, unsigned long long* out)
+{
+    __shared__ unsigned long long s[4][8];
+    unsigned long long v[4] = {~0ull, ~0ull, 0ull, 0ull};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double a = q[2 * (size_t)i], b = q[2 * (size_t)i + 1];
-        v[0] = fmin(v[0], a); v[1] = fmin(v[1], b); v[2] = fmax(v[2], a); v[3] = fmax(v[3], b);
+        if (a == a) {
+            const unsigned long long k = dkey(a);
+            v[0] = min(v[0], k);
+            v[2] = max(v[2], k);
+        }
+        if (b == b) {
+            const unsigned long long k = dkey(b);
+            v[1] = min(v[1], k);
+            v[3] = max(v[3], k);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-        v[1] = fmin(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
-        v[2] = fmax(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
-        v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+        v[0] = min(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = min(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] = max(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
+        v[3] = max(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
     }
     if ((threadIdx.x & 31) == 0)
         for (int k = 0; k < 4; ++k) s[k][threadIdx.x >> 5] = v[k];
     __syncthreads();
     if (threadIdx.x < 4) {
-        double r = threadIdx.x < 2 ? INFINITY : -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            r = threadIdx.x < 2 ? fmin(r, s[threadIdx.x][w]) : fmax(r, s[threadIdx.x][w]);
-        out[threadIdx.x] = r;
+        const int k = threadIdx.x;
+        unsigned long long r = s[k][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = k < 2 ? min(r, s[k][w]) : max(r, s[k][w]);
+        if (k < 2) atomicMin(out + k, r);
+        else atomicMax(out + k, r);
     }
 }
 
@@ -595,11 +624,19 @@ ep_status load_anchor(const ep_params& P, CellBufs& b, const double* q, const do
 {
     Impl* im = impl_of(b);
     const int n = b.n;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(im->bbox);
+    EP_TRY_CUDA(cudaMemsetAsync(keys, 0xFF, 2 * sizeof(unsigned long long), st));
+    EP_TRY_CUDA(cudaMemsetAsync(keys + 2, 0, 2 * sizeof(unsigned long long), st));
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    const int nbb = std::max(1, std::min((n + 255) / 256, 2 * di.sm_count));
     count_launch();
-    k_bbox2<<<1, 1024, 0, st>>>(q, n, im->bbox);
-    double bb[4];
-    EP_TRY_CUDA(cudaMemcpyAsync(bb, im->bbox, sizeof bb, cudaMemcpyDeviceToHost, st));
+    k_bbox2<<<nbb, 256, 0, st>>>(q, n, keys);
+    unsigned long long kb[4];
+    EP_TRY_CUDA(cudaMemcpyAsync(kb, keys, sizeof kb, cudaMemcpyDeviceToHost, st));
     EP_TRY_CUDA(cudaStreamSynchronize(st));
+    double bb[4];
+    for (int k = 0; k < 4; ++k) bb[k] = dkey_value(kb[k]);
     im->g = make_grid(bb, P.sigma);
     im->cur = 0;
     EP_TRY_CUDA(cudaMemsetAsync(im->count[0], 0, sizeof(int) * (size_t)im->g.ncell, st));

@@ -129,3 +129,29 @@ def test_cell_list_is_deterministic():
     a = ep.shoot(cuda(pr.X), cuda(p), prm)[0]
     b = ep.shoot(cuda(pr.X), cuda(p), prm)[0]
     assert torch.equal(a, b)
+
+
+def test_shoot_with_large_motion():
+    # momenta large enough to carry particles more than a cell edge: particles change
+    # cells many times along the shoot (and some leave the starting grid's interior)
+    pr, p = grid_problem(40)
+    p = 80.0 * p
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, steps=20, precision=ep.MIXED, neigh=ep.CELLLIST)
+    q1, p1 = ep.shoot(cuda(pr.X), cuda(p), prm)
+    rq, rp = o.shoot(pr.X, p, ep.TENT, pr.sigma, 20)
+    assert np.abs(rq - pr.X).max() > 1.2 * pr.sigma
+    assert rel(q1, rq) < 1e-3 and rel(p1, rp) < 1e-3
+
+
+def test_dense_cluster_beyond_the_staging_capacity():
+    # 2500 particles within 0.6 sigma of each other, in a few cells: more records than
+    # a sweep block stages in shared memory, so the sweep reads them from global memory
+    rng = np.random.default_rng(5)
+    sigma = 0.05
+    ang, rad = rng.uniform(0, 2 * np.pi, 2500), 0.3 * sigma * np.sqrt(rng.uniform(0, 1, 2500))
+    X = 0.5 + np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+    p = rng.normal(0, 1e-4, size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=sigma, steps=4, precision=ep.MIXED, neigh=ep.CELLLIST)
+    q1, p1 = ep.shoot(cuda(X), cuda(p), prm)
+    rq, rp = o.shoot(X, p, ep.TENT, sigma, 4)
+    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-3
