@@ -39,7 +39,7 @@ namespace ep {
 
 namespace {
 
-constexpr int kCluster = 8;
+constexpr int kCluster = 4;
 constexpr int kThreads = 1024;
 constexpr int kMaxN = 8192;          // particles per problem (shared-memory records)
 constexpr int kMaxPerThread = 2;     // particles i per thread and CTA slice
@@ -96,12 +96,14 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 
-__device__ __forceinline__ void kfun(int ker, float r2, float& G, float& w)
+// G and the momentum weight w of one pair at scaled squared distance r2.
+template <int KER>
+__device__ __forceinline__ void kfun(float r2, float& G, float& w)
 {
-    if (ker == EP_GAUSS) {
+    if constexpr (KER == EP_GAUSS) {
         G = ex2_approx(-r2);
         w = G;
-    } else if (ker == EP_TENT) {
+    } else if constexpr (KER == EP_TENT) {
         const float rs = rsqrt_approx(fmaxf(r2, 1e-30f));
         const bool in = r2 < 1.0f;
         G = in ? fmaf(-r2, rs, 1.0f) : 0.0f;
@@ -111,6 +113,22 @@ __device__ __forceinline__ void kfun(int ker, float r2, float& G, float& w)
         G = ex2_approx(-r2 * rs);
         w = G * rs;
     }
+}
+
+// One pair term of Eq. N-particle added to the FP32 sums s = (dq_x, dq_y, m_x, m_y)
+// of particle ri (the momentum sum before its dp_scale factor).
+template <int KER>
+__device__ __forceinline__ void pair_term(const float4& ri, const float4& rj, float (&s)[4])
+{
+    const float dx = ri.x - rj.x, dy = ri.y - rj.y;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    float G, w;
+    kfun<KER>(r2, G, w);
+    s[0] = fmaf(G, rj.z, s[0]);
+    s[1] = fmaf(G, rj.w, s[1]);
+    const float c = w * fmaf(ri.z, rj.z, ri.w * rj.w);
+    s[2] = fmaf(c, dx, s[2]);
+    s[3] = fmaf(c, dy, s[3]);
 }
 
 // Team context: the CTAs that solve one problem together.
@@ -164,59 +182,94 @@ __device__ __forceinline__ int slot_particle(int lo, int L, int r)
 
 // Pair sums over all n sources in shared memory for the thread's particles
 // (slot r: particle slot_particle(lo, L, r) if < hi); k = (dq, dp) per particle,
-// complete in every lane of the particle's lane group.
-__device__ void pair_sums(const float4* rec, int n, int lo, int hi, int L, int ker, float dp_scale,
-                          float (&kq)[kMaxPerThread][2], float (&kp)[kMaxPerThread][2])
+// complete in every lane of the particle's lane group.  Each particle's sum runs
+// over its sources in increasing order (FP32 partial sums per run of kFold
+// sources, added in FP64 when there are several: FP64 costs ~60 FP32 issue slots
+// per warp here).  When a thread holds two particles (L = 1 and a slice of more
+// than kThreads), both take each staged record from one shared-memory load.
+template <int KER>
+__device__ void pair_sums_k(const float4* rec, int n, int lo, int hi, int L, float dp_scale,
+                            float (&kq)[kMaxPerThread][2], float (&kp)[kMaxPerThread][2])
 {
+    static_assert(kMaxPerThread == 2, "the paired loop holds two particles");
     const int sub = (int)threadIdx.x % L;
+    const bool multi = n > kFold;
 #pragma unroll
-    for (int r = 0; r < kMaxPerThread; ++r) {
-        const int i = slot_particle(lo, L, r);
-        kq[r][0] = kq[r][1] = kp[r][0] = kp[r][1] = 0.f;
-        if (r > 0 && L > 1) continue;     // lane groups hold one particle each
-        const bool on = i < hi;
-        // FP32 partial sums per run of kFold sources; runs are added in FP64 only when
-        // there is more than one (FP64 costs ~60 FP32 issue slots per warp here)
-        const bool multi = n > kFold;
-        float q0 = 0.f, q1 = 0.f, p0 = 0.f, p1 = 0.f;
-        double aq0 = 0, aq1 = 0, ap0 = 0, ap1 = 0;
-        if (on) {
-            const float4 ri = rec[i];
-            for (int j0 = 0; j0 < n; j0 += kFold) {
-                const int j1 = min(n, j0 + kFold);
-                for (int j = j0 + sub; j < j1; j += L) {
-                    const float4 rj = rec[j];
-                    const float dx = ri.x - rj.x, dy = ri.y - rj.y;
-                    const float r2 = fmaf(dx, dx, dy * dy);
-                    float G, w;
-                    kfun(ker, r2, G, w);
-                    q0 = fmaf(G, rj.z, q0);
-                    q1 = fmaf(G, rj.w, q1);
-                    const float c = w * fmaf(ri.z, rj.z, ri.w * rj.w);
-                    p0 = fmaf(c, dx, p0);
-                    p1 = fmaf(c, dy, p1);
-                }
-                if (multi) {
-                    aq0 += q0; aq1 += q1; ap0 += p0; ap1 += p1;
-                    q0 = q1 = p0 = p1 = 0.f;
+    for (int r = 0; r < kMaxPerThread; ++r) kq[r][0] = kq[r][1] = kp[r][0] = kp[r][1] = 0.f;
+    if (L == 1 && hi - lo > kThreads) {
+        const int i0 = slot_particle(lo, 1, 0), i1 = slot_particle(lo, 1, 1);
+        const bool on0 = i0 < hi, on1 = i1 < hi;
+        if (!on0) return;
+        const float4 r0 = rec[i0], r1 = rec[on1 ? i1 : i0];
+        float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
+        double d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0};
+        for (int j0 = 0; j0 < n; j0 += kFold) {
+            const int j1 = min(n, j0 + kFold);
+#pragma unroll 2
+            for (int j = j0; j < j1; ++j) {
+                const float4 rj = rec[j];
+                pair_term<KER>(r0, rj, s0);
+                pair_term<KER>(r1, rj, s1);
+            }
+            if (multi) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    d0[c] += s0[c];
+                    d1[c] += s1[c];
+                    s0[c] = s1[c] = 0.f;
                 }
             }
         }
-        if (multi) {
-            q0 = (float)aq0; q1 = (float)aq1; p0 = (float)ap0; p1 = (float)ap1;
+        if (multi)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                s0[c] = (float)d0[c];
+                s1[c] = (float)d1[c];
+            }
+        kq[0][0] = s0[0]; kq[0][1] = s0[1]; kp[0][0] = dp_scale * s0[2]; kp[0][1] = dp_scale * s0[3];
+        if (on1) {
+            kq[1][0] = s1[0]; kq[1][1] = s1[1]; kp[1][0] = dp_scale * s1[2]; kp[1][1] = dp_scale * s1[3];
         }
-        // combine the lane group in FP32 (whole groups are active or inactive together)
-        for (int o = L >> 1; o > 0; o >>= 1) {
-            q0 += __shfl_xor_sync(0xffffffffu, q0, o);
-            q1 += __shfl_xor_sync(0xffffffffu, q1, o);
-            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
-            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-        }
-        kq[r][0] = q0;
-        kq[r][1] = q1;
-        kp[r][0] = dp_scale * p0;
-        kp[r][1] = dp_scale * p1;
+        return;
     }
+    // one particle per lane group (slot 0)
+    const int i = slot_particle(lo, L, 0);
+    float sm[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < hi) {
+        const float4 ri = rec[i];
+        double acc[4] = {0, 0, 0, 0};
+        for (int j0 = 0; j0 < n; j0 += kFold) {
+            const int j1 = min(n, j0 + kFold);
+#pragma unroll 4
+            for (int j = j0 + sub; j < j1; j += L) pair_term<KER>(ri, rec[j], sm);
+            if (multi) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc[c] += sm[c];
+                    sm[c] = 0.f;
+                }
+            }
+        }
+        if (multi)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sm[c] = (float)acc[c];
+    }
+    // combine the lane group in FP32 (whole groups are active or inactive together)
+    for (int o = L >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sm[c] += __shfl_xor_sync(0xffffffffu, sm[c], o);
+    kq[0][0] = sm[0];
+    kq[0][1] = sm[1];
+    kp[0][0] = dp_scale * sm[2];
+    kp[0][1] = dp_scale * sm[3];
+}
+
+__device__ __forceinline__ void pair_sums(const float4* rec, int n, int lo, int hi, int L, int ker, float dp_scale,
+                                          float (&kq)[kMaxPerThread][2], float (&kp)[kMaxPerThread][2])
+{
+    if (ker == EP_GAUSS) pair_sums_k<EP_GAUSS>(rec, n, lo, hi, L, dp_scale, kq, kp);
+    else if (ker == EP_TENT) pair_sums_k<EP_TENT>(rec, n, lo, hi, L, dp_scale, kq, kp);
+    else pair_sums_k<EP_EXPCONE>(rec, n, lo, hi, L, dp_scale, kq, kp);
 }
 
 // Write one record into the shared memory of every CTA of the team.
