@@ -237,10 +237,13 @@ __device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int co
         const float y = fmaf(comp < 2 ? cdt * a.s_f : cdt, kv, e.xs);
         *A = a.stage == 0 ? kv : fmaf(2.0f, kv, e.A);  // k1 + 2 k2 + 2 k3
         reinterpret_cast<float*>(a.S_out + i)[comp] = y;
+        if (a.rec_out) reinterpret_cast<float*>(a.rec_out + i)[comp] = y;
     } else {
         const double nv = e.xv + (double)(a.dt_f * (1.0f / 6.0f) * (e.A + kv));
         *epi_state(a, i, comp) = nv;
-        reinterpret_cast<float*>(a.Sx_w + i)[comp] = comp < 2 ? (float)((nv - a.c0[comp]) * a.s) : (float)nv;
+        const float w = comp < 2 ? (float)((nv - a.c0[comp]) * a.s) : (float)nv;
+        reinterpret_cast<float*>(a.Sx_w + i)[comp] = w;
+        if (a.rec_out) reinterpret_cast<float*>(a.rec_out + i)[comp] = w;
     }
 }
 
@@ -571,10 +574,12 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
     }
 }
 
-// The owner-computes shoot (mode RK4: `steps` steps) or one RHS (mode RHS, input Sx).
-template <int THREADS, int JL>
+// The owner-computes shoot (mode RK4: `steps` steps) or one RHS (mode RHS, input Sx);
+// REC: every stage output is also written to the recording rec.
+template <int THREADS, int JL, bool REC>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_shoot_owner(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
+    k_shoot_owner(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err,
+                  float4* rec)
 {
     extern __shared__ float4 smem[];
     const int n = a.n;
@@ -587,6 +592,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         a.stage = stage;
         a.S_in = a.mode == MODE_RHS || stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
         a.S_out = stage == 1 ? Sb : Sa;
+        a.rec_out = REC ? rec + (size_t)(st + 1) * n : nullptr;  // stage input st + 1 of a recorded shoot
         stage_owner_gauss2<THREADS, JL>(a, smem, r0, r1);
         if (st + 1 < nst && !grid_barrier(bar, err, ++epoch)) return;
     }
@@ -605,7 +611,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_stage_mixed(StageArgs a)
 // of the particles this CTA owns ([c n / G, (c+1) n / G)), and a barrier.
 template <int DIM, int KER, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_shoot_mixed(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
+    k_shoot_mixed(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err,
+                  float4* rec)
 {
     extern __shared__ float4 smem[];
     const int n = a.n;
@@ -617,6 +624,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             a.stage = stage;
             a.S_in = stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
             a.S_out = stage == 1 ? Sb : Sa;
+            a.rec_out = rec ? rec + (size_t)(4 * s + stage + 1) * (DIM == 2 ? 1 : 2) * n : nullptr;
             stage_pairs<DIM, KER, THREADS, false>(a, smem, nullptr);
             if (!grid_barrier(bar, err, ++epoch)) return;
             for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<DIM>(a, i);
@@ -631,7 +639,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // owns, and a barrier.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_shoot_streamk(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err)
+    k_shoot_streamk(StageArgs a, const float4* Sx, float4* Sa, float4* Sb, int steps, unsigned* bar, int* err,
+                    float4* rec)
 {
     extern __shared__ float4 smem[];
     const int n = a.n;
@@ -643,6 +652,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             a.stage = stage;
             a.S_in = stage == 0 ? Sx : (stage == 2 ? Sb : Sa);
             a.S_out = stage == 1 ? Sb : Sa;
+            a.rec_out = rec ? rec + (size_t)(4 * s + stage + 1) * n : nullptr;
             stage_pairs_gauss2<THREADS>(a, smem);
             if (!grid_barrier(bar, err, ++epoch)) return;
             for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<2>(a, i);
@@ -1101,7 +1111,7 @@ ep_status finish_persistent(const AllPairsBufs& b, cudaStream_t st, bool* done)
 
 template <int DIM, int KER>
 ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
-                             cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
+                             cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, float4* rec = nullptr)
 {
     constexpr int THREADS = 1024;
     constexpr int W = THREADS / 32;
@@ -1126,7 +1136,7 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
     unsigned* bar = b.bar;
     int* err = b.err;
     EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
-    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err, &rec};
     count_launch();
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
@@ -1142,31 +1152,32 @@ struct OwnerCfg {
 
 template <int JL>
 ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
-                       cudaEvent_t ev0, cudaEvent_t ev1)
+                       cudaEvent_t ev0, cudaEvent_t ev1, float4* rec)
 {
     constexpr int THREADS = 1024;
     const size_t smem = owner_smem<THREADS, JL>();
-    auto fn = k_shoot_owner<THREADS, JL>;
-    static int resident = -1;
-    if (resident < 0) {
+    auto fn = rec ? k_shoot_owner<THREADS, JL, true> : k_shoot_owner<THREADS, JL, false>;
+    static int resident[2] = {-1, -1};
+    int& res = resident[rec ? 1 : 0];
+    if (res < 0) {
         EP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, smem));
         DeviceInfo di{};
         EP_TRY(device_info(&di));
-        resident = per_sm * di.sm_count;
+        res = per_sm * di.sm_count;
     }
     *done = false;
     StageArgs a = a0;
     a.G = std::max(1, std::min(a.G, a.n));
-    if (a.G > resident) return EP_OK;
+    if (a.G > res) return EP_OK;
     const float4* Sx = b.Sx;
     float4* Sa = b.Sa;
     float4* Sb = b.Sb;
     unsigned* bar = b.bar;
     int* err = b.err;
     EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
-    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err, &rec};
     count_launch();
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
@@ -1176,7 +1187,7 @@ ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cu
 
 // The stream-K 2-D Gaussian shoot over a.G CTAs (tiles of kTileG).
 ep_status launch_streamk(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
-                         cudaEvent_t ev0, cudaEvent_t ev1)
+                         cudaEvent_t ev0, cudaEvent_t ev1, float4* rec)
 {
     constexpr int THREADS = 1024;
     constexpr int W = THREADS / 32;
@@ -1203,7 +1214,7 @@ ep_status launch_streamk(const StageArgs& a0, const AllPairsBufs& b, int steps, 
     unsigned* bar = b.bar;
     int* err = b.err;
     EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
-    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err};
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err, &rec};
     count_launch();
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
@@ -1213,14 +1224,14 @@ ep_status launch_streamk(const StageArgs& a0, const AllPairsBufs& b, int steps, 
 
 // JL = 1, 4, 16: owner computes with that many source lanes; JL = 0: stream-K.
 ep_status launch_owner_cfg(const StageArgs& a, const AllPairsBufs& b, int steps, const OwnerCfg& c, cudaStream_t st,
-                           bool* done, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
+                           bool* done, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, float4* rec = nullptr)
 {
     StageArgs a2 = a;
     a2.G = c.G;
-    if (c.JL == 0) return launch_streamk(a2, b, steps, st, done, ev0, ev1);
-    if (c.JL == 1) return launch_owner<1>(a2, b, steps, st, done, ev0, ev1);
-    if (c.JL == 16) return launch_owner<16>(a2, b, steps, st, done, ev0, ev1);
-    return launch_owner<4>(a2, b, steps, st, done, ev0, ev1);
+    if (c.JL == 0) return launch_streamk(a2, b, steps, st, done, ev0, ev1, rec);
+    if (c.JL == 1) return launch_owner<1>(a2, b, steps, st, done, ev0, ev1, rec);
+    if (c.JL == 16) return launch_owner<16>(a2, b, steps, st, done, ev0, ev1, rec);
+    return launch_owner<4>(a2, b, steps, st, done, ev0, ev1, rec);
 }
 
 // Default owner configuration: the widest sub-tile the rows per SM fill, and the
@@ -1237,10 +1248,10 @@ OwnerCfg owner_default(int n, int sm)
 }
 
 ep_status launch_shoot(const ep_params& P, const StageArgs& a, const AllPairsBufs& b, int steps, cudaStream_t st,
-                       bool* done, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
+                       bool* done, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, float4* rec = nullptr)
 {
 #define EP_SHOOT_CASE(D, K) \
-    if (P.dim == D && P.kernel == K) return launch_shoot_mixed<D, K>(a, b, steps, st, done, ev0, ev1);
+    if (P.dim == D && P.kernel == K) return launch_shoot_mixed<D, K>(a, b, steps, st, done, ev0, ev1, rec);
     EP_SHOOT_CASE(2, EP_TENT) EP_SHOOT_CASE(2, EP_EXPCONE)
     EP_SHOOT_CASE(3, EP_GAUSS) EP_SHOOT_CASE(3, EP_TENT) EP_SHOOT_CASE(3, EP_EXPCONE)
 #undef EP_SHOOT_CASE
@@ -1370,6 +1381,63 @@ struct TimedLaunch {
     }
 };
 
+// The persistent (one cooperative launch) shoot of mixed precision, when it
+// applies: tuned owner / stream-K / tensor-core launch for the 2-D Gaussian, the
+// generic persistent shoot otherwise.  rec: if set, every stage input is also
+// written to the recording (stage copy k + 1 after stage k; copy 0 is the caller's);
+// the tensor-core path does not record.  *done = false when no persistent launch ran.
+ep_status persistent_steps(const ep_params& P, const AllPairsBufs& b, StageArgs a, int steps, double dt,
+                           cudaStream_t st, float4* rec, bool* done)
+{
+    *done = false;
+    const APConfig cfg = allpairs_config(b.n, P.dim, P.precision, P.kernel);
+    if (!(P.precision == EP_MIXED && cfg.threads == 1024 && allpairs_persistent_enabled())) return EP_OK;
+    a.Sx_w = b.Sx;
+    if (P.dim == 2 && P.kernel == EP_GAUSS) {
+        const bool tc = !rec && tc_enabled(P) && b.part;
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        OwnerCfg c = tc ? OwnerCfg{di.sm_count, 0} : owner_default(b.n, di.sm_count);
+        if (b.x_bak && autotune_enabled()) {
+            const TuneKey key{b.n, P.dim, P.kernel, di.device, tc ? 1 : 0};
+            bool have = false;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) c = it->second, have = true;
+            }
+            if (!have) {
+                EP_TRY(tune_persistent(P, b, a, dt, st, &c, tc));
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tuned[key] = c;
+            }
+        }
+        TimedLaunch tl;
+        char name[64];
+        if (tc) {
+            EP_TRY(tc_run(P, b, steps, dt, MODE_RK4, nullptr, nullptr, c.G, st, tl.e0, tl.e1));
+            *done = true;
+            snprintf(name, sizeof(name), "k_shoot_tc (G=%d)", c.G);
+        } else {
+            EP_TRY(launch_owner_cfg(a, b, steps, c, st, done, tl.e0, tl.e1, rec));
+            if (c.JL == 0)
+                snprintf(name, sizeof(name), "k_shoot_streamk<1024> (G=%d)", c.G);
+            else
+                snprintf(name, sizeof(name), "k_shoot_owner<1024,%d> (G=%d)", c.JL, std::min(c.G, b.n));
+        }
+        if (*done) tl.record(name);
+        return EP_OK;
+    }
+    TimedLaunch tl;
+    EP_TRY(launch_shoot(P, a, b, steps, st, done, tl.e0, tl.e1, rec));
+    if (*done) {
+        char name[64];
+        snprintf(name, sizeof(name), "k_shoot_mixed<%d,%d,1024> (G=%d)", P.dim, P.kernel, a.G);
+        tl.record(name);
+    }
+    return EP_OK;
+}
+
 ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, double dt, cudaStream_t st)
 {
     if (b.n == 0 || steps == 0) return EP_OK;
@@ -1378,57 +1446,9 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
     a.mode = MODE_RK4;
     a.dt = dt;
     a.dt_f = (float)dt;
-    if (P.precision == EP_MIXED && cfg.threads == 1024 && allpairs_persistent_enabled()) {
-        a.Sx_w = b.Sx;
-        if (P.dim == 2 && P.kernel == EP_GAUSS) {
-            const bool tc = tc_enabled(P) && b.part;
-            DeviceInfo di{};
-            EP_TRY(device_info(&di));
-            OwnerCfg c = tc ? OwnerCfg{di.sm_count, 0} : owner_default(b.n, di.sm_count);
-            if (b.x_bak && autotune_enabled()) {
-                const TuneKey key{b.n, P.dim, P.kernel, di.device, tc ? 1 : 0};
-                bool have = false;
-                {
-                    std::lock_guard<std::mutex> lk(g_tune_mu);
-                    auto it = g_tuned.find(key);
-                    if (it != g_tuned.end()) c = it->second, have = true;
-                }
-                if (!have) {
-                    EP_TRY(tune_persistent(P, b, a, dt, st, &c, tc));
-                    std::lock_guard<std::mutex> lk(g_tune_mu);
-                    g_tuned[key] = c;
-                }
-            }
-            TimedLaunch tl;
-            bool done = false;
-            char name[64];
-            if (tc) {
-                EP_TRY(tc_run(P, b, steps, dt, MODE_RK4, nullptr, nullptr, c.G, st, tl.e0, tl.e1));
-                done = true;
-                snprintf(name, sizeof(name), "k_shoot_tc (G=%d)", c.G);
-            } else {
-                EP_TRY(launch_owner_cfg(a, b, steps, c, st, &done, tl.e0, tl.e1));
-                if (c.JL == 0)
-                    snprintf(name, sizeof(name), "k_shoot_streamk<1024> (G=%d)", c.G);
-                else
-                    snprintf(name, sizeof(name), "k_shoot_owner<1024,%d> (G=%d)", c.JL, std::min(c.G, b.n));
-            }
-            if (done) {
-                tl.record(name);
-                return EP_OK;
-            }
-        } else {
-            TimedLaunch tl;
-            bool done = false;
-            EP_TRY(launch_shoot(P, a, b, steps, st, &done, tl.e0, tl.e1));
-            if (done) {
-                char name[64];
-                snprintf(name, sizeof(name), "k_shoot_mixed<%d,%d,1024> (G=%d)", P.dim, P.kernel, a.G);
-                tl.record(name);
-                return EP_OK;
-            }
-        }
-    }
+    bool done = false;
+    EP_TRY(persistent_steps(P, b, a, steps, dt, st, nullptr, &done));
+    if (done) return EP_OK;
     a.Sx = b.Sx;
     a.Sx_w = b.Sx;
     for (int s = 0; s < steps; ++s) {
@@ -1465,6 +1485,11 @@ ep_status allpairs_steps_rec(const ep_params& P, const AllPairsBufs& b, int step
         EP_TRY_CUDA(cudaMemcpyAsync(rec, b.Sx, sizeof(float4) * cm, cudaMemcpyDeviceToDevice, st));
     else
         EP_TRY_CUDA(cudaMemcpyAsync(drec, b.Dx, sizeof(double) * cd, cudaMemcpyDeviceToDevice, st));
+    if (P.precision == EP_MIXED) {
+        bool done = false;
+        EP_TRY(persistent_steps(P, b, a, steps, dt, st, rec, &done));
+        if (done) return EP_OK;
+    }
     for (int k = 0; k < steps; ++k) {
         for (int stage = 0; stage < 4; ++stage) {
             a.stage = stage;

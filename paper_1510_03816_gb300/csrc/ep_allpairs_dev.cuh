@@ -27,6 +27,7 @@ struct StageArgs {
     float4* S_out;
     const float4* Sx;   // step-start stage copy (mixed)
     float4* Sx_w;       // written at stage 3 (mixed)
+    float4* rec_out;    // if set, a second copy of the stage output (mixed; a recorded shoot)
     const double* D_in; // fp64 stage copies
     double* D_out;
     double* x;
@@ -189,9 +190,14 @@ __device__ void epilogue_mixed_k(const StageArgs& a, int i, const double* kk)
         }
         if constexpr (DIM == 2) {
             a.S_out[i] = make_float4(y[0], y[1], y[2], y[3]);
+            if (a.rec_out) a.rec_out[i] = make_float4(y[0], y[1], y[2], y[3]);
         } else {
             a.S_out[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
             a.S_out[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
+            if (a.rec_out) {
+                a.rec_out[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
+                a.rec_out[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
+            }
         }
     } else {
         // x_{n+1} = x_n + dt/6 (k1 + 2 k2 + 2 k3 + k4): the increment in FP32, the state in FP64
@@ -210,9 +216,14 @@ __device__ void epilogue_mixed_k(const StageArgs& a, int i, const double* kk)
         }
         if constexpr (DIM == 2) {
             a.Sx_w[i] = make_float4(y[0], y[1], y[2], y[3]);
+            if (a.rec_out) a.rec_out[i] = make_float4(y[0], y[1], y[2], y[3]);
         } else {
             a.Sx_w[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
             a.Sx_w[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
+            if (a.rec_out) {
+                a.rec_out[2 * (size_t)i] = make_float4(y[0], y[1], y[2], 0.0f);
+                a.rec_out[2 * (size_t)i + 1] = make_float4(y[3], y[4], y[5], 0.0f);
+            }
         }
     }
 }
