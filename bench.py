@@ -71,7 +71,49 @@ def parse():
                     help="only run warmup + steps shoots of the workload (for ncu captures); no JSON line")
     ap.add_argument("--profile-rk4-steps", type=int, default=0,
                     help="with --profile: RK4 steps per shoot (0 = the workload's 100), for short captures")
+    ap.add_argument("--profile-row", default="", choices=["", "cell_list", "batched", "tangent", "match_fp64",
+                                                           "velocity"],
+                    help="run one small case of that secondary row (for ncu captures); no JSON line")
     return ap.parse_args()
+
+
+def profile_row(name: str) -> None:
+    """One small case of a secondary row, for a short ncu capture of its kernel:
+    cell_list  the 512 x 512 jittered-grid tent shoot, 1 RK4 step (k_cell_sweep)
+    batched    37 circle -> ellipse problems of n = 4096, alternating tent and Gaussian, 5 steps, 2 shoots
+    tangent    the N = 1024 Fourier-curve tangent shoot, FP64, 5 steps (k_tangent_fp64)
+    match_fp64 the N = 64 circle -> ellipse FP64 match, 5 updates (k_match_fp64)
+    velocity   the same with the velocity update, 3 updates (MINRES inside k_match_fp64)"""
+    import torch
+    from paper_1510_03816_gb300 import ep, workloads
+
+    ep.load()
+    dev = "cuda"
+    if name == "cell_list":
+        g = workloads.jittered_grid()
+        prm = ep.params(dim=2, kernel=ep.TENT, sigma=g.sigma, steps=1, precision=ep.MIXED, neigh=ep.CELLLIST)
+        ep.shoot(torch.tensor(g.X, device=dev), torch.tensor(0.01 * (g.Y - g.X), device=dev), prm)
+    elif name == "batched":
+        probs = [workloads.circle_to_ellipse(n=4096, kernel=ep.TENT if b % 2 == 0 else ep.GAUSS,
+                                             sigma=0.2 if b % 2 == 0 else 0.1, steps=5) for b in range(37)]
+        prms = [ep.params(dim=2, kernel=p.kernel, sigma=p.sigma, steps=p.steps, precision=ep.MIXED) for p in probs]
+        ep.match_batched([torch.tensor(p.X, device=dev) for p in probs], [torch.tensor(p.Y, device=dev) for p in probs],
+                         prms, h=0.0, eps=1e-12, maxit=1)
+    elif name == "tangent":
+        f = workloads.fourier_curve_warp(n=1024, steps=5)
+        X = torch.tensor(f.X, device=dev)
+        v = torch.tensor(np.random.default_rng(3).normal(size=f.X.shape), device=dev)
+        prm = ep.params(dim=2, kernel=f.kernel, sigma=f.sigma, steps=f.steps, precision=ep.FP64, neigh=ep.ALLPAIRS)
+        ep.shoot_tangent(X, 0.002 * (torch.tensor(f.Y, device=dev) - X), torch.zeros_like(X), v, prm)
+    else:
+        c = workloads.circle_to_ellipse()
+        prm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.FP64, neigh=ep.ALLPAIRS)
+        X, Y = torch.tensor(c.X, device=dev), torch.tensor(c.Y, device=dev)
+        if name == "match_fp64":
+            ep.match(X, Y, prm, h=0.0, eps=0.0, maxit=5)
+        else:
+            ep.match(X, Y, prm, h=0.5, eps=0.0, maxit=3, rule=ep.RULE_VELOCITY)
+    torch.cuda.synchronize()
 
 
 def dist_setup(args):
@@ -587,6 +629,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.profile_row:
+        profile_row(args.profile_row)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
