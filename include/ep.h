@@ -64,7 +64,10 @@ typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
  * Both solved rules are FP64, all-pairs, exact system only (EP_EINVAL otherwise).
  * The velocity rule runs inside the device-resident matching launch: MINRES on the
  * symmetric G(X) (the tent's need not be positive definite), one all-pairs Gram
- * product per iteration.  The Newton rule runs restarted GMRES on the host
+ * product per iteration.  The Newton rule forms D phi whole on the device (one
+ * tangent-linear shoot per column, all in one launch) and solves it by Gaussian
+ * elimination with partial pivoting when n dim <= 384 (a singular D phi returns
+ * EP_EDIVERGED); larger problems run restarted GMRES on the host
  * (ep_match_info.krylov vectors) whose products are tangent-linear shoots along
  * (0, v) on the device (ep_shoot_tangent). */
 typedef enum { EP_RULE_MOMENTUM = 0, EP_RULE_VELOCITY = 1, EP_RULE_NEWTON = 2 } ep_rule;
@@ -102,8 +105,9 @@ typedef struct {
     int krylov;      /* in: Krylov size of the solved rules (0 = min(n dim, 200)): the GMRES
                         restart length (Newton); the inner solve (GMRES or MINRES) stops at
                         relative residual 1e-12 or after 4 krylov products */
-    int products;    /* out: matrix-vector products of the solved rules (tangent shoots or
-                        Gram products) over the whole matching; 0 for the momentum rule */
+    int products;    /* out: matrix-vector products of the solved rules over the whole
+                        matching (tangent shoots: Jacobian columns or Krylov products;
+                        Gram products); 0 for the momentum rule */
 } ep_match_info;
 
 /* Right-hand side of the N-particle system (Sec. 3.1, Eq. N-particle):

@@ -21,9 +21,14 @@
 // (D phi) delta = r by restarted GMRES whose matrix-vector products are tangent
 // shoots along (0, v) (matrix-free: D phi = dQ(1)/dp0 is never formed), and
 // updates p0 += h delta.  The Krylov basis lives on the host (n dim doubles per
-// vector); each product is one launch.
+// vector); each product is one launch.  Problems with n dim <= kDenseNewtonMax form
+// D phi whole instead (one CTA per column, all columns in one launch) and solve it
+// by Gaussian elimination with partial pivoting on one CTA; the residual and the
+// update stay on the device.
 #include <math.h>
 #include <stdint.h>
+
+#include <string.h>
 
 #include <algorithm>
 #include <cmath>
@@ -172,6 +177,255 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_fp64(TanArgs a)
             a.out[(size_t)i * DIM + c] = v;
         else
             a.out[nd + (size_t)i * DIM + (c - DIM)] = v;
+    }
+}
+
+// ------------------------------------------------------------------ dense Newton (small n)
+// For n dim <= kDenseNewtonMax the Jacobian D phi = dQ(1)/dp0 is formed column by
+// column in one launch: CTA c integrates the tangent shoot along (0, e_c) over all
+// particles itself (its tangent state in shared memory, __syncthreads between
+// stages, no grid-wide barrier), so the n dim directions run on that many SMs at
+// once.  One CTA then solves (D phi) delta = r by Gaussian elimination with
+// partial pivoting.
+constexpr int kDenseNewtonMax = 384;
+constexpr int kJacThreads = 256;
+
+struct JacArgs {
+    int n, steps;
+    double dt, sigma;
+    const double* drec;  // (4 steps + 1) primal stage copies, (q, p) = 2 dim doubles per particle
+    double* J;           // n dim x n dim, column-major: J[c N + r] = d Q(1)_r / d p0_c
+};
+
+// Warp sum of V <= 8 doubles, reduce-scatter form; afterwards lane l holds the total
+// of value first(l) and the lanes with (l & (32 / P - 1)) == 0 hold distinct values.
+template <int V>
+__device__ __forceinline__ double warp_sum_scatter(double (&v)[V], int& first)
+{
+    constexpr int P = V == 1 ? 1 : V == 2 ? 2 : V <= 4 ? 4 : 8;
+    const int lane = threadIdx.x & 31;
+    double u[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) u[k] = k < V ? v[k] : 0.0;
+    first = 0;
+    int cnt = P;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (cnt > 1) {
+            const int h = cnt / 2;
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < P / 2; ++k) {
+                if (k < h) {
+                    const double send = upper ? u[k] : u[k + h];
+                    const double keep = upper ? u[k + h] : u[k];
+                    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            if (upper) first += h;
+            cnt = h;
+        } else {
+            u[0] += __shfl_xor_sync(0xffffffffu, u[0], o);
+        }
+    }
+    return u[0];
+}
+
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kJacThreads) k_jac_fp64(JacArgs a)
+{
+    constexpr int S2 = 2 * DIM;
+    constexpr int P = S2 <= 4 ? 4 : 8;
+    extern __shared__ double js[];
+    const int n = a.n;
+    const int N = n * DIM;
+    const int c = blockIdx.x;  // direction (0, e_c)
+    const size_t sn = (size_t)S2 * n;
+    double* T0 = js;           // tangent stage inputs (ping-pong)
+    double* T1 = js + sn;
+    double* X0 = js + 2 * sn;  // tangent state at the step start
+    double* A = js + 3 * sn;   // tangent RK4 accumulator
+    for (int t = threadIdx.x; t < (int)sn; t += kJacThreads) {
+        const int i = t / S2, k = t % S2;
+        const double v = (k >= DIM && i * DIM + (k - DIM) == c) ? 1.0 : 0.0;
+        T0[t] = v;
+        X0[t] = v;
+        A[t] = 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int W = kJacThreads / 32;
+    double* Tin = T0;
+    double* Tout = T1;
+    for (int k = 0; k < a.steps; ++k) {
+        for (int s = 0; s < 4; ++s) {
+            const double* Y = a.drec + (size_t)(4 * k + s) * sn;
+            for (int i = warp; i < n; i += W) {
+                double qi[DIM], pi[DIM], vqi[DIM], vpi[DIM];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    qi[d] = __ldg(Y + (size_t)i * S2 + d);
+                    pi[d] = __ldg(Y + (size_t)i * S2 + DIM + d);
+                    vqi[d] = Tin[i * S2 + d];
+                    vpi[d] = Tin[i * S2 + DIM + d];
+                }
+                double h[S2];
+#pragma unroll
+                for (int u = 0; u < S2; ++u) h[u] = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    double dd[DIM], dv[DIM], pj[DIM], vpj[DIM];
+                    double r2 = 0.0, ddv = 0.0, pp = 0.0, a1 = 0.0;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        dd[d] = qi[d] - __ldg(Y + (size_t)j * S2 + d);
+                        dv[d] = vqi[d] - Tin[j * S2 + d];
+                        pj[d] = __ldg(Y + (size_t)j * S2 + DIM + d);
+                        vpj[d] = Tin[j * S2 + DIM + d];
+                        r2 += dd[d] * dd[d];
+                        ddv += dd[d] * dv[d];
+                        pp += pi[d] * pj[d];
+                        a1 += vpi[d] * pj[d] + pi[d] * vpj[d];
+                    }
+                    double G, phi, psi;
+                    kfun3_f64<KER>(r2, a.sigma, G, phi, psi);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) h[d] += G * vpj[d] + phi * ddv * pj[d];
+                    if (j != i) {
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d) h[DIM + d] += a1 * phi * dd[d] + pp * (phi * dv[d] + psi * ddv * dd[d]);
+                    }
+                }
+                int first;
+                const double tot = warp_sum_scatter<S2>(h, first);
+                // the tangent RK4 stage of component `first` of row i, dk = (h_p, -h_q)
+                if ((lane & (32 / P - 1)) == 0 && first < S2) {
+                    const int e = i * S2 + first;
+                    const double dk = first < DIM ? tot : -tot;
+                    if (s < 3) {
+                        const double cdt = (s == 2 ? 1.0 : 0.5) * a.dt;
+                        Tout[e] = X0[e] + cdt * dk;
+                        A[e] = s == 0 ? dk : A[e] + 2.0 * dk;
+                    } else {
+                        const double nv = X0[e] + a.dt / 6.0 * (A[e] + dk);
+                        X0[e] = nv;
+                        Tout[e] = nv;
+                    }
+                }
+            }
+            __syncthreads();
+            double* tmp = Tin;
+            Tin = Tout;
+            Tout = tmp;
+        }
+    }
+    // column c of D phi: the position part of the tangent at t1
+    for (int r = threadIdx.x; r < N; r += kJacThreads) a.J[(size_t)c * N + r] = X0[(r / DIM) * S2 + (r % DIM)];
+}
+
+// r = Y - Q(1) (Q(1): the first m entries of the step state) and the max-norm of r
+// by atomicMax on the IEEE bits (non-finite values rank above every finite one).
+__global__ void k_residual(const double* __restrict__ Y, const double* __restrict__ Q1, int m, double* __restrict__ r,
+                           unsigned long long* res_bits)
+{
+    unsigned long long mb = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+        const double v = Y[e] - Q1[e];
+        r[e] = v;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+        mb = b > mb ? b : mb;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = u > mb ? u : mb;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(res_bits, mb);
+}
+
+__global__ void k_axpy_update(double* __restrict__ p, const double* __restrict__ delta, double h, int m)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) p[e] += h * delta[e];
+}
+
+// Solve J x = b (J column-major N x N, overwritten by its LU factors; b overwritten by
+// x) by Gaussian elimination with partial pivoting (the largest |pivot| in the
+// column, the first on ties), one CTA.  *singular = 1 when a pivot is zero.
+constexpr int kLuThreads = 512;
+__global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restrict__ J, double* __restrict__ b,
+                                                        int* singular)
+{
+    __shared__ double s_val[kLuThreads / 32];
+    __shared__ int s_idx[kLuThreads / 32];
+    __shared__ int s_piv;
+    __shared__ double s_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int W = kLuThreads / 32;
+    auto at = [&](int r, int c) -> double& { return J[(size_t)c * N + r]; };
+    for (int k = 0; k < N; ++k) {
+        // pivot row: max |J(r, k)| over r >= k
+        double best = -1.0;
+        int bi = N;
+        for (int r = k + threadIdx.x; r < N; r += kLuThreads) {
+            const double v = fabs(at(r, k));
+            if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = s_val[0];
+            int bix = s_idx[0];
+            for (int w = 1; w < W; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bix)) { bv = s_val[w]; bix = s_idx[w]; }
+            s_piv = bix;
+            if (!(bv > 0.0)) *singular = 1;
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr >= N) return;  // no pivot at all (all entries NaN): the flag is raised
+        // swap rows k and pr over columns k..N-1 and b
+        if (pr != k) {
+            for (int c = k + threadIdx.x; c <= N; c += kLuThreads) {
+                double* x = c < N ? &at(k, c) : &b[k];
+                double* y = c < N ? &at(pr, c) : &b[pr];
+                const double t = *x;
+                *x = *y;
+                *y = t;
+            }
+        }
+        __syncthreads();
+        const double piv = at(k, k);
+        if (piv == 0.0) continue;
+        // multipliers, then the trailing update (column c, rows > k) and b
+        for (int r = k + 1 + threadIdx.x; r < N; r += kLuThreads) at(r, k) /= piv;
+        __syncthreads();
+        const int rows = N - k - 1;
+        for (int t = threadIdx.x; t < rows * (N - k); t += kLuThreads) {
+            const int r = k + 1 + t % rows, c = k + 1 + t / rows;  // c == N: the right-hand side
+            if (c < N) at(r, c) -= at(r, k) * at(k, c);
+            else b[r] -= at(r, k) * b[k];
+        }
+        __syncthreads();
+    }
+    // back substitution
+    for (int k = N - 1; k >= 0; --k) {
+        double sum = 0.0;
+        for (int c = k + 1 + threadIdx.x; c < N; c += kLuThreads) sum += at(k, c) * b[c];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) s_val[warp] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tsum = 0.0;
+            for (int w = 0; w < W; ++w) tsum += s_val[w];
+            const double d = at(k, k);
+            s_x = d != 0.0 ? (b[k] - tsum) / d : 0.0;
+            b[k] = s_x;
+        }
+        __syncthreads();
     }
 }
 
@@ -437,9 +691,16 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     if (P.inexact != 0.0) return set_error("ep_match: the Newton gain is built for the exact system"), EP_EINVAL;
     if (info->krylov < 0) return set_error("ep_match: krylov must be >= 0"), EP_EINVAL;
     const size_t m = (size_t)n * P.dim;
+    // small problems form D phi whole (one CTA per column) and solve it densely
+    const bool dense = m <= (size_t)kDenseNewtonMax;
     Sizer z;
     z.add(tan_bytes(n, P.dim, P.steps));
     z.add(sizeof(double) * m * 6);
+    if (dense) {
+        z.add(sizeof(double) * m * m);
+        z.add(sizeof(double) * m * 2);
+        z.add(64);
+    }
     Arena* ar = nullptr;
     EP_TRY(arena_acquire(st, z.total, &ar));
     TanBufs t;
@@ -449,6 +710,18 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     double* dk = (double*)ar->carve(sizeof(double) * m);
     double* dd = (double*)ar->carve(sizeof(double) * m);
     if (!dd) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+    double *dJ = nullptr, *dY = nullptr, *dr = nullptr;
+    unsigned long long* dres = nullptr;
+    int* dsing = nullptr;
+    if (dense) {
+        dJ = (double*)ar->carve(sizeof(double) * m * m);
+        dY = (double*)ar->carve(sizeof(double) * m);
+        dr = (double*)ar->carve(sizeof(double) * m);
+        dres = (unsigned long long*)ar->carve(64);
+        if (!dres) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+        dsing = (int*)(dres + 4);
+        EP_TRY(copy_in(dY, Y, m, st));
+    }
     EP_TRY(copy_in(dX, X, m, st));
     EP_TRY(copy_in(dp, p0, m, st));
     std::vector<double> hY(m), hp(m), hq(m), r(m), delta;
@@ -473,17 +746,31 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     ep_status status = EP_ENOTCONVERGED;
     int k = 0;
     double res = 0.0;
+    bool singular = false;
     for (;;) {
         // Q(1): the step state x of the all-pairs buffers after the recorded shoot
         EP_TRY(tan_record(P, t, dX, dp, st));
-        EP_TRY_CUDA(cudaMemcpyAsync(hq.data(), t.ap.x, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-        EP_TRY_CUDA(cudaStreamSynchronize(st));
-        res = 0.0;
         bool finite = true;
-        for (size_t a = 0; a < m; ++a) {
-            r[a] = hY[a] - hq[a];
-            if (!std::isfinite(r[a])) finite = false;
-            res = std::max(res, fabs(r[a]));
+        if (dense) {
+            // r = Y - Q(1) and |r|_inf on the device
+            unsigned long long rb = 0;
+            EP_TRY_CUDA(cudaMemsetAsync(dres, 0, sizeof(unsigned long long), st));
+            count_launch();
+            k_residual<<<(unsigned)std::min<size_t>((m + 255) / 256, 1024), 256, 0, st>>>(dY, t.ap.x, (int)m, dr, dres);
+            EP_TRY_CUDA(cudaGetLastError());
+            EP_TRY_CUDA(cudaMemcpyAsync(&rb, dres, sizeof rb, cudaMemcpyDeviceToHost, st));
+            EP_TRY_CUDA(cudaStreamSynchronize(st));
+            finite = rb < 0x7FF0000000000000ull;
+            memcpy(&res, &rb, sizeof res);
+        } else {
+            EP_TRY_CUDA(cudaMemcpyAsync(hq.data(), t.ap.x, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            EP_TRY_CUDA(cudaStreamSynchronize(st));
+            res = 0.0;
+            for (size_t a = 0; a < m; ++a) {
+                r[a] = hY[a] - hq[a];
+                if (!std::isfinite(r[a])) finite = false;
+                res = std::max(res, fabs(r[a]));
+            }
         }
         if (!finite) res = NAN;
         if (info->hist) {
@@ -504,6 +791,42 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
             status = EP_ENOTCONVERGED;
             break;
         }
+        if (dense) {
+            // D phi by columns (one tangent shoot per CTA), then (D phi) delta = r, p0 += h delta
+            JacArgs ja{};
+            ja.n = (int)n;
+            ja.steps = P.steps;
+            ja.dt = P.t1 / P.steps;
+            ja.sigma = P.sigma;
+            ja.drec = t.drec;
+            ja.J = dJ;
+            const size_t smem = sizeof(double) * 4 * 2 * (size_t)P.dim * n;
+            ep_status ls = EP_EINVAL;
+#define EP_JAC_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) { count_launch(); k_jac_fp64<D, K><<<(unsigned)m, kJacThreads, smem, st>>>(ja); ls = EP_OK; }
+            EP_JAC_CASE(2, EP_GAUSS) EP_JAC_CASE(2, EP_TENT) EP_JAC_CASE(2, EP_EXPCONE)
+            EP_JAC_CASE(3, EP_GAUSS) EP_JAC_CASE(3, EP_TENT) EP_JAC_CASE(3, EP_EXPCONE)
+#undef EP_JAC_CASE
+            if (ls != EP_OK) return set_error("ep_match: no Jacobian kernel for this kernel"), ls;
+            EP_TRY_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int), st));
+            count_launch(2);
+            k_lu_solve<<<1, kLuThreads, 0, st>>>((int)m, dJ, dr, dsing);
+            k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dr, h, (int)m);
+            EP_TRY_CUDA(cudaGetLastError());
+            int sing = 0;
+            EP_TRY_CUDA(cudaMemcpyAsync(&sing, dsing, sizeof(int), cudaMemcpyDeviceToHost, st));
+            EP_TRY_CUDA(cudaStreamSynchronize(st));
+            info->products += (int)m;
+            ++k;
+            if (sing) {
+                set_error("ep_match: the shooting Jacobian is singular after %d updates", k);
+                singular = true;
+                status = EP_EDIVERGED;
+                res = NAN;
+                break;
+            }
+            continue;
+        }
         int used = 0;
         EP_TRY(gmres(apply, r, delta, krylov, maxprod, kKrylovTol, &used));
         info->products += used;
@@ -514,6 +837,7 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     info->iters = k;
     info->resid_inf = res;
     EP_TRY_CUDA(cudaMemcpyAsync(p0, dp, sizeof(double) * m, cudaMemcpyDefault, st));
+    if (dense) EP_TRY_CUDA(cudaMemcpyAsync(hp.data(), dp, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
     // H(X, p0) of Eq. H: 1/2 sum_i p_i . dq_i
     EP_TRY(allpairs_load(P, t.ap, dX, dp, st));
     EP_TRY(allpairs_rhs(P, t.ap, dk, dd, st));
@@ -524,7 +848,7 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     for (size_t a = 0; a < m; ++a) H += 0.5 * hp[a] * hdq[a];
     info->H = H;
     if (status == EP_ENOTCONVERGED) set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", k, res, info->eps);
-    if (status == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", k);
+    if (status == EP_EDIVERGED && !singular) set_error("ep_match: residual became non-finite after %d updates", k);
     return status;
 }
 

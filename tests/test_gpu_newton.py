@@ -171,3 +171,30 @@ def test_rule_refusals():
     with pytest.raises(ep.EPError):
         ep.shoot_tangent(X, X, X, X, ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.MIXED,
                                                neigh=ep.ALLPAIRS))
+
+
+def test_newton_rule_krylov_path_parity():
+    # n dim = 420 > 384: the Newton update runs restarted GMRES over tangent shoots instead
+    # of the dense Jacobian; two updates compared iterate by iterate (cond D phi ~ 3)
+    X = np.stack(np.meshgrid(np.arange(14), np.arange(15)), -1).reshape(-1, 2) * 0.04 + 0.2
+    Y = X + 0.002 * np.random.default_rng(42).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.02, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_NEWTON, h=1.0, eps=0.0, maxit=2)
+    rp, st, it, r, hist = o.match_newton(X, Y, ep.GAUSS, 0.02, 4, h=1.0, eps=0.0, maxit=2)
+    assert res.status == st == ep.ENOTCONVERGED and res.iters == it == 2
+    assert rel(res.p0, rp) < 1e-8
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-6)
+    assert res.products > 2 * 10  # Krylov products, not dense columns (2 x 420)
+    assert res.products != 2 * X.size
+
+
+def test_newton_rule_dense_path_counts_columns():
+    # n dim = 24 <= 384: each update forms the whole Jacobian, n dim tangent shoots
+    pr = w.circle_to_ellipse(12, sigma=0.1, kernel=ep.GAUSS, steps=10)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(pr.X, pr.Y, prm, ep.RULE_NEWTON, h=1.0, eps=0.0, maxit=3)
+    rp, st, it, r, hist = o.match_newton(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=1.0, eps=0.0, maxit=3)
+    assert res.iters == it == 3 and res.products == 3 * 24
+    assert rel(res.p0, rp) < 1e-9
+    big = hist > 1e-6
+    np.testing.assert_allclose(res.hist[big], hist[big], rtol=1e-6)
