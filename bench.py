@@ -549,8 +549,8 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
         dt = time.perf_counter() - t0
         note = (f"host GMRES; each of the {r.products} tangent shoots is one cooperative launch of 200 "
                 "dependent FP64 stages on 64 particles" if rule == ep.RULE_NEWTON else
-                f"one cooperative launch: 43 shoots of 200 dependent FP64 stages and {r.products} MINRES "
-                "iterations (stored G(X) product, two grid sums, three grid barriers each)")
+                f"one cooperative launch: 43 shoots of 200 dependent FP64 stages; G(X) factored once "
+                f"(LU, one CTA), then {r.products} forward/back substitutions (one warp each)")
         out[name] = {"workload": f"circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, FP64, h={h}, "
                                  + ("Newton gain h (D phi)^-1" if rule == ep.RULE_NEWTON else "velocity update "
                                     "h G(X)^-1 r"),

@@ -62,9 +62,10 @@ typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
  *  EP_RULE_NEWTON    p0 += h (D phi)^-1 r      the gain M = h (D phi)^-1 of Theorem 1,
  *                                              D phi = dQ(1)/dp0 of the RK4 shoot
  * Both solved rules are FP64, all-pairs, exact system only (EP_EINVAL otherwise).
- * The velocity rule runs inside the device-resident matching launch: MINRES on the
- * symmetric G(X) (the tent's need not be positive definite), one all-pairs Gram
- * product per iteration.  The Newton rule forms D phi whole on the device (one
+ * The velocity rule runs inside the device-resident matching launch: for n <= 512
+ * it factors G(X) once (LU with partial pivoting) and solves each update with the
+ * factors; otherwise (or when a pivot vanishes) MINRES on the symmetric G(X) (the
+ * tent's need not be positive definite), one all-pairs Gram product per iteration.  The Newton rule forms D phi whole on the device (one
  * tangent-linear shoot per column, all in one launch) and solves it by Gaussian
  * elimination with partial pivoting when n dim <= 384 (a singular D phi returns
  * EP_EDIVERGED); larger problems run restarted GMRES on the host
@@ -106,8 +107,10 @@ typedef struct {
                         restart length (Newton); the inner solve (GMRES or MINRES) stops at
                         relative residual 1e-12 or after 4 krylov products */
     int products;    /* out: matrix-vector products of the solved rules over the whole
-                        matching (tangent shoots: Jacobian columns or Krylov products;
-                        Gram products); 0 for the momentum rule */
+                        matching: tangent shoots (Jacobian columns or Krylov products) for
+                        Newton; MINRES Gram products, or one solve per component and
+                        update with the factored G(X), for the velocity rule; 0 for the
+                        momentum rule */
 } ep_match_info;
 
 /* Right-hand side of the N-particle system (Sec. 3.1, Eq. N-particle):

@@ -291,6 +291,90 @@ __device__ __forceinline__ void cta_sum_f64(double (&v)[V], double* sm)
     for (int k = 0; k < V; ++k) v[k] = sm[W * P + k];
 }
 
+// Dense LU factorisation with partial pivoting by one CTA of THREADS threads:
+// A (N x N, column-major, A[c N + r]) is overwritten by L (unit lower, below the
+// diagonal) and U; piv[k] = the row swapped with row k at step k (the largest
+// |pivot| in the column, the first on ties).  Returns false (in every thread) when a
+// pivot is zero or no pivot is finite.  scratch: 2 * THREADS / 32 + 2 words of
+// shared memory.
+template <int THREADS>
+__device__ bool cta_lu_factor(int N, double* A, int* piv, double* s_val, int* s_idx)
+{
+    constexpr int W = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool ok = true;
+    for (int k = 0; k < N; ++k) {
+        double best = -1.0;
+        int bi = N;
+        for (int r = k + (int)threadIdx.x; r < N; r += THREADS) {
+            const double v = fabs(A[(size_t)k * N + r]);
+            if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bv = s_val[0];
+            int bix = s_idx[0];
+            for (int w = 1; w < W; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] < bix)) { bv = s_val[w]; bix = s_idx[w]; }
+            s_idx[W] = bv > 0.0 ? bix : -1;
+        }
+        __syncthreads();
+        const int pr = s_idx[W];
+        if (pr < 0) { ok = false; break; }  // uniform: every thread read the same slot
+        if (threadIdx.x == 0) piv[k] = pr;
+        if (pr != k)
+            for (int c = (int)threadIdx.x; c < N; c += THREADS) {
+                const double t = A[(size_t)c * N + k];
+                A[(size_t)c * N + k] = A[(size_t)c * N + pr];
+                A[(size_t)c * N + pr] = t;
+            }
+        __syncthreads();
+        const double d = A[(size_t)k * N + k];
+        for (int r = k + 1 + (int)threadIdx.x; r < N; r += THREADS) A[(size_t)k * N + r] /= d;
+        __syncthreads();
+        const int rows = N - k - 1;
+        for (int t = (int)threadIdx.x; t < rows * rows; t += THREADS) {
+            const int r = k + 1 + t % rows, c = k + 1 + t / rows;
+            A[(size_t)c * N + r] -= A[(size_t)k * N + r] * A[(size_t)c * N + k];
+        }
+        __syncthreads();
+    }
+    return ok;
+}
+
+// Solve A x = b with the factors of cta_lu_factor (b overwritten by x) by one warp:
+// the row swaps, forward substitution with the unit L, back substitution with U,
+// each step's dot product split over the lanes and summed by shuffles.
+__device__ void warp_lu_solve(int N, const double* A, const int* piv, double* b)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < N; ++k) {
+            const int p = piv[k];
+            if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+        }
+    __syncwarp();
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int s = 0; s < N; ++s) {
+            const int k = pass == 0 ? s : N - 1 - s;
+            double sum = 0.0;
+            if (pass == 0)
+                for (int c = lane; c < k; c += 32) sum += A[(size_t)c * N + k] * b[c];
+            else
+                for (int c = k + 1 + lane; c < N; c += 32) sum += A[(size_t)c * N + k] * b[c];
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) b[k] = pass == 0 ? b[k] - sum : (b[k] - sum) / A[(size_t)k * N + k];
+            __syncwarp();
+        }
+    }
+}
+
 // Grid-wide barrier of a cooperative launch (all CTAs resident).  The counter
 // only grows: barrier number e completes when it reaches e * gridDim.x.  The
 // wait is bounded; on giving up it raises the shared error flag, and every CTA

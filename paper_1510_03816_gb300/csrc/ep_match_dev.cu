@@ -22,6 +22,10 @@
 // owned rows (G(X) v over all sources), two grid-wide sums (v . z and |z|^2, as
 // per-CTA partials that every CTA adds in the same order, so all CTAs hold the same
 // scalars) and the publication of the next Lanczos vector: three grid barriers.
+// For n <= kGramLuMaxN, CTA 0 instead factors G(X) once (LU with partial pivoting,
+// G(X) being symmetric and fixed for the whole matching) and each update is a
+// forward and a back substitution per component by one warp; MINRES remains the
+// solver when a pivot vanishes.
 //
 // FP64 on this GPU runs at 1/64 of the FP32 rate, so a small problem's FP64 pair
 // work is spread over as many SMs as there are particles (up to the SM count);
@@ -39,6 +43,7 @@ namespace ep {
 namespace {
 
 constexpr int kMatchThreads = 256;
+constexpr int kGramLuMaxN = 512;  // the velocity rule factors G(X) up to this many landmarks
 
 struct MatchArgs {
     int n, steps, maxit;
@@ -62,6 +67,8 @@ struct MatchArgs {
     double* Z;                 // G(X) v - beta v_old (own rows)
     double* Del;               // the MINRES iterate delta (own rows)
     double* Gm;                // G(X), n x n row-major (own rows written), or null: evaluate per pair
+    int* piv;                  // pivots of the LU factors of G(X) (n <= kGramLuMaxN)
+    int* lu_ok;                // 1 when CTA 0 factored G(X) (then the updates solve with the factors)
     double* out;               // h, residual, H, iterations, status, Gram products
     unsigned* bar;
     int* err;
@@ -324,6 +331,17 @@ __global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
                 kfun_f64<KER>(r2, a.sigma, G, phi);
                 a.Gm[(size_t)i * n + j] = G;
             }
+        if (a.piv) {
+            // every row of G(X) written, then CTA 0 factors it (symmetric: the row-major
+            // rows are the column-major columns); the other CTAs go on to the first shoot
+            if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+            if (blockIdx.x == 0) {
+                __shared__ double s_lv[kMatchThreads / 32 + 1];
+                __shared__ int s_li[kMatchThreads / 32 + 1];
+                const bool ok = cta_lu_factor<kMatchThreads>(n, a.Gm, a.piv, s_lv, s_li);
+                if (threadIdx.x == 0) *a.lu_ok = ok ? 1 : 0;
+            }
+        }
     }
     if (!(h > 0.0)) {
         // the stage copy D[0] holds (X, 1) for the row sums
@@ -408,6 +426,27 @@ __global__ void __launch_bounds__(kMatchThreads) k_match_fp64(MatchArgs a)
         if (!finite) { status = EP_EDIVERGED; break; }
         if (a.s2 == 0.0 && res < a.eps) { status = EP_OK; break; }
         if (k == a.maxit) { status = EP_ENOTCONVERGED; break; }
+        if (a.rule == EP_RULE_VELOCITY && a.piv && __ldcg(a.lu_ok) == 1) {
+            // G(X) delta = r with the factors: CTA 0, one warp, one component at a time
+            if (blockIdx.x == 0 && threadIdx.x < 32) {
+                for (int c = 0; c < DIM; ++c) {
+                    double* bc = a.Z + (size_t)c * n;
+                    for (int i = threadIdx.x; i < n; i += 32)
+                        bc[i] = __ldcg(a.Y + (size_t)i * DIM + c) - __ldcg(a.x + (size_t)i * DIM + c);
+                    __syncwarp();
+                    warp_lu_solve(n, a.Gm, a.piv, bc);
+                    for (int i = threadIdx.x; i < n; i += 32) a.Del[(size_t)i * DIM + c] = bc[i];
+                    __syncwarp();
+                }
+            }
+            products += DIM;
+            if (!grid_barrier(a.bar, a.err, ++epoch)) return;
+            for (int t = threadIdx.x; t < (r1 - r0) * DIM; t += kMatchThreads) {
+                const size_t e = (size_t)r0 * DIM + t;
+                a.p0[e] += h * __ldcg(a.Del + e);
+            }
+            continue;
+        }
         if (a.rule == EP_RULE_VELOCITY) {
             const int used = minres_gram<DIM, KER>(a, r0, r1, sm_d, epoch);
             if (used < 0) return;
@@ -493,6 +532,10 @@ size_t match_device_bytes(int64_t n, int dim, int maxit, int rule)
     z.add(sizeof(double) * 1024);           // per-CTA partials
     for (int k = 0; k < 7; ++k) z.add(sizeof(double) * m);  // MINRES vectors
     if (rule == EP_RULE_VELOCITY && n <= kGramStoreMaxN) z.add(sizeof(double) * (size_t)n * n);  // G(X)
+    if (rule == EP_RULE_VELOCITY && n <= kGramLuMaxN) {
+        z.add(sizeof(int) * (size_t)n);  // pivots
+        z.add(sizeof(int) * 4);          // factorisation flag
+    }
     z.add(sizeof(double) * 8);              // outputs
     z.add(sizeof(unsigned) * 12);           // barrier + error flag
     return z.total;
@@ -533,6 +576,12 @@ ep_status match_device_fp64(const ep_params& P, int64_t n, const double* X, cons
     a.Del = (double*)ar->carve(sizeof(double) * m);
     a.Gm = a.rule == EP_RULE_VELOCITY && n <= kGramStoreMaxN ? (double*)ar->carve(sizeof(double) * (size_t)n * n)
                                                                : nullptr;
+    if (a.Gm && n <= kGramLuMaxN) {
+        a.piv = (int*)ar->carve(sizeof(int) * (size_t)n);
+        a.lu_ok = (int*)ar->carve(sizeof(int) * 4);
+        if (!a.lu_ok) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+        EP_TRY_CUDA(cudaMemsetAsync(a.lu_ok, 0, sizeof(int) * 4, st));
+    }
     a.out = (double*)ar->carve(sizeof(double) * 8);
     a.bar = (unsigned*)ar->carve(sizeof(unsigned) * 12);
     if (!a.bar) return set_error("ep_match: workspace too small"), EP_ENOMEM;

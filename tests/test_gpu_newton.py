@@ -198,3 +198,43 @@ def test_newton_rule_dense_path_counts_columns():
     assert rel(res.p0, rp) < 1e-9
     big = hist > 1e-6
     np.testing.assert_allclose(res.hist[big], hist[big], rtol=1e-6)
+
+
+# --------------------------------------------------------------------------- the benchmark's configurations
+
+
+def test_newton_bench_workload():
+    # the bench row: circle -> ellipse, 64 landmarks, tent sigma = 0.25, 50 steps, h = 1, eps = 1e-6
+    c = w.circle_to_ellipse()
+    prm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(c.X, c.Y, prm, ep.RULE_NEWTON, h=1.0, eps=c.eps, maxit=c.maxit)
+    rp, st, it, r, hist = o.match_newton(c.X, c.Y, c.kernel, c.sigma, c.steps, h=1.0, eps=c.eps, maxit=c.maxit)
+    assert res.status == st == ep.OK and res.iters == it
+    assert rel(res.p0, rp) < 1e-7
+    big = hist > 1e-6
+    np.testing.assert_allclose(res.hist[big], hist[big], rtol=1e-6)
+
+
+def test_velocity_rule_bench_workload():
+    # the bench row: the same workload with the velocity update, h = 0.5
+    c = w.circle_to_ellipse()
+    prm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(c.X, c.Y, prm, ep.RULE_VELOCITY, h=0.5, eps=c.eps, maxit=c.maxit)
+    rp, st, it, r, hist = o.match_velocity(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.5, eps=c.eps, maxit=c.maxit)
+    assert res.status == st == ep.OK
+    assert abs(res.iters - it) <= 1
+    k = min(len(res.hist), len(hist))
+    np.testing.assert_allclose(res.hist[:k], hist[:k], rtol=1e-6, atol=1e-12)
+
+
+def test_tangent_shoot_bench_workload():
+    # the bench row: N = 1024 Fourier curve, Gaussian sigma = 0.1, 50 steps, direction (0, v)
+    f = w.fourier_curve_warp(n=1024, steps=50)
+    p0 = 0.002 * (f.Y - f.X)
+    v = np.random.default_rng(3).normal(size=f.X.shape)
+    z = np.zeros_like(f.X)
+    prm = ep.params(dim=2, kernel=f.kernel, sigma=f.sigma, steps=50, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    q1, p1, vq1, vp1 = ep.shoot_tangent(cuda(f.X), cuda(p0), cuda(z), cuda(v), prm)
+    rq, rp, rvq, rvp = o.shoot_tangent(f.X, p0, z, v, f.kernel, f.sigma, 50)
+    assert rel(q1, rq) < 1e-12 and rel(p1, rp) < 1e-11
+    assert rel(vq1, rvq) < 1e-10 and rel(vp1, rvp) < 1e-10
