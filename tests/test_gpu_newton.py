@@ -238,3 +238,17 @@ def test_tangent_shoot_bench_workload():
     rq, rp, rvq, rvp = o.shoot_tangent(f.X, p0, z, v, f.kernel, f.sigma, 50)
     assert rel(q1, rq) < 1e-12 and rel(p1, rp) < 1e-11
     assert rel(vq1, rvq) < 1e-10 and rel(vp1, rvp) < 1e-10
+
+
+def test_velocity_rule_minres_path():
+    # n = 624 > 512: G(X) is not factored and every update runs MINRES inside the launch
+    # (tent sigma = 0.03 on a 0.025 grid: cond G(X) ~ 5); two updates, iterate by iterate
+    X = np.stack(np.meshgrid(np.arange(26), np.arange(24)), -1).reshape(-1, 2) * 0.025 + 0.2
+    Y = X + 0.002 * np.random.default_rng(7).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=0.03, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_VELOCITY, h=0.5, eps=0.0, maxit=2)
+    rp, st, it, r, hist = o.match_velocity(X, Y, ep.TENT, 0.03, 4, h=0.5, eps=0.0, maxit=2)
+    assert res.iters == it == 2
+    assert res.products > 2 * 2  # MINRES Gram products, not one solve per component and update
+    assert rel(res.p0, rp) < 1e-9
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-9)
