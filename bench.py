@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--profile-rk4-steps", type=int, default=0,
                     help="with --profile: RK4 steps per shoot (0 = the workload's 100), for short captures")
     ap.add_argument("--profile-row", default="", choices=["", "cell_list", "batched", "tangent", "match_fp64",
-                                                           "velocity"],
+                                                           "velocity", "adjoint"],
                     help="run one small case of that secondary row (for ncu captures); no JSON line")
     return ap.parse_args()
 
@@ -86,13 +86,19 @@ def profile_row(name: str) -> None:
     batched    37 circle -> ellipse problems of n = 4096, alternating tent and Gaussian, 5 steps, 2 shoots
     tangent    the N = 1024 Fourier-curve tangent shoot, FP64, 5 steps (k_tangent_fp64)
     match_fp64 the N = 64 circle -> ellipse FP64 match, 5 updates (k_match_fp64)
-    velocity   the same with the velocity update, 3 updates (MINRES inside k_match_fp64)"""
+    velocity   the same with the velocity update, 3 updates (factored G(X) inside k_match_fp64)
+    adjoint    one gradient of the N = 16384 3-D star-surface workload (100 steps, checkpoints every 10)"""
     import torch
     from paper_1510_03816_gb300 import ep, workloads
 
     ep.load()
     dev = "cuda"
-    if name == "cell_list":
+    if name == "adjoint":
+        a3 = workloads.star_surface_3d()
+        X3, Y3, p3 = (torch.tensor(v, device=dev) for v in (a3.X, a3.Y, a3.p0))
+        prm3 = ep.params(dim=3, kernel=ep.GAUSS, sigma=a3.sigma, steps=a3.steps, precision=ep.MIXED)
+        ep.adjoint(X3, p3, Y3, prm3, a3.lam, 10)
+    elif name == "cell_list":
         g = workloads.jittered_grid()
         prm = ep.params(dim=2, kernel=ep.TENT, sigma=g.sigma, steps=1, precision=ep.MIXED, neigh=ep.CELLLIST)
         ep.shoot(torch.tensor(g.X, device=dev), torch.tensor(0.01 * (g.Y - g.X), device=dev), prm)
