@@ -42,6 +42,10 @@ def cuda(a):
     return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
 
 
+def host(a):
+    return a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+
+
 def cloud(n, dim, seed, sigma=None, band=1e-9):
     """Positions in [0.2, 0.8]^dim with no pair distance within band of the tent's kink."""
     rng = np.random.default_rng(seed)
@@ -252,3 +256,30 @@ def test_velocity_rule_minres_path():
     assert res.products > 2 * 2  # MINRES Gram products, not one solve per component and update
     assert rel(res.p0, rp) < 1e-9
     np.testing.assert_allclose(res.hist, hist, rtol=1e-9)
+
+
+# --------------------------------------------------------------------------- degenerate cases
+
+
+@pytest.mark.parametrize("rule", [ep.RULE_NEWTON, ep.RULE_VELOCITY])
+def test_rules_one_particle_land_in_one_step(rule):
+    # one Gaussian particle: Q(1) = X + p0, so D phi = I and G(X) = [1]: a full step lands
+    X, Y = np.array([[0.3, 0.4]]), np.array([[0.35, 0.42]])
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=5, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, rule, h=1.0, eps=1e-13, maxit=5)
+    assert res.status == ep.OK and res.iters == 1 and res.resid < 1e-15
+    np.testing.assert_allclose(host(res.p0), Y - X, rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("rule", [ep.RULE_NEWTON, ep.RULE_VELOCITY])
+def test_rules_no_update_and_converged_start(rule):
+    pr = w.circle_to_ellipse(12, sigma=0.1, kernel=ep.GAUSS, steps=10)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    # maxit = 0: one shoot, no update, the residual of p0 = 0 is max |Y - X|
+    res = _match(pr.X, pr.Y, prm, rule, h=1.0, eps=0.0, maxit=0)
+    assert res.status == ep.ENOTCONVERGED and res.iters == 0 and res.products == 0
+    assert res.resid == pytest.approx(np.abs(pr.Y - pr.X).max(), rel=1e-15)
+    np.testing.assert_array_equal(host(res.p0), 0.0)
+    # Y = X: converged before any update
+    res = _match(pr.X, pr.X, prm, rule, h=1.0, eps=1e-12, maxit=5)
+    assert res.status == ep.OK and res.iters == 0 and res.resid == 0.0
