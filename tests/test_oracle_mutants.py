@@ -76,3 +76,79 @@ def test_pins_reject_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins accepted the mutant {name}:\n{r.stdout[-2000:]}"
+
+
+# --------------------------------------------------------------------------- the update rules (Python)
+# The velocity update and the Newton loop are Python around library solves; each case
+# plants one plausible mistake in a copy of the oracle module (same C library) and runs
+# the pins of the rules against it in this process.
+import importlib
+import inspect
+import itertools
+import types
+
+ORACLE_PY = os.path.join(ROOT, "oracle", "oracle.py")
+
+PY_MUTANTS = {
+    "velocity_multiplies_by_gram": ("p = p + h * np.linalg.solve(GX, r)", "p = p + h * (GX @ r)"),
+    "velocity_update_sign": ("p = p + h * np.linalg.solve(GX, r)", "p = p - h * np.linalg.solve(GX, r)"),
+    "velocity_drops_gain": ("p = p + h * np.linalg.solve(GX, r)", "p = p + np.linalg.solve(GX, r)"),
+    "newton_transposed_jacobian": ("p = p + h * np.linalg.solve(J, r.ravel()).reshape(n, dim)",
+                                   "p = p + h * np.linalg.solve(J.T, r.ravel()).reshape(n, dim)"),
+    "newton_update_sign": ("p = p + h * np.linalg.solve(J, r.ravel()).reshape(n, dim)",
+                           "p = p - h * np.linalg.solve(J, r.ravel()).reshape(n, dim)"),
+    "newton_identity_gain": ("p = p + h * np.linalg.solve(J, r.ravel()).reshape(n, dim)",
+                             "p = p + h * r"),
+}
+
+
+def _rule_pins():
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    pins = importlib.import_module("test_oracle_pins")
+    names = [k for k in dir(pins) if k.startswith("test_") and ("velocity_rule" in k or "newton" in k)]
+    return pins, names
+
+
+def _calls(fn):
+    marks = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+    if not marks:
+        yield {}
+        return
+    keys, values = [], []
+    for m in marks:
+        keys.append([s.strip() for s in m.args[0].split(",")])
+        values.append(m.args[1])
+    for combo in itertools.product(*values):
+        kw = {}
+        for ks, v in zip(keys, combo):
+            kw.update({ks[0]: v} if len(ks) == 1 else dict(zip(ks, v)))
+        yield kw
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_rule_pins_reject_mutant(name):
+    old, new = PY_MUTANTS[name]
+    src = open(ORACLE_PY).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique in oracle.py"
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = ORACLE_PY
+    exec(compile(src.replace(old, new), ORACLE_PY, "exec"), mod.__dict__)
+    pins, names = _rule_pins()
+    real = pins.o
+    failed = False
+    try:
+        pins.o = mod
+        for nm in names:
+            fn = getattr(pins, nm)
+            for kw in _calls(fn):
+                try:
+                    fn(**kw)
+                except Exception:
+                    failed = True
+                    break
+            if failed:
+                break
+    finally:
+        pins.o = real
+    assert failed, f"the rule pins accepted the mutant {name}"
+    assert inspect.ismodule(mod)

@@ -615,3 +615,21 @@ def test_velocity_rule_converges_on_a_noise_free_tent_problem():
     assert st == o.OK and it < 60
     r = np.array(hist)
     assert np.all(r[-5:] / r[-6:-1] < 0.7)
+
+
+def test_newton_step_solves_the_linearised_shooting_equation():
+    # From a momentum large enough that D phi is far from symmetric (|J - J^T| ~ 0.9 |J|),
+    # the Newton step delta must solve the linearised equation D phi delta = r, checked
+    # with the plain shoot alone: (Q(1; p + t delta) - Q(1; p - t delta)) / 2t = r + O(t^2)
+    pr = w.circle_to_ellipse(12, sigma=0.15, kernel=o.GAUSS, steps=10)
+    pbar = 0.3 * np.random.default_rng(5).normal(size=pr.X.shape)
+    p1 = o.match_newton(pr.X, pr.Y, o.GAUSS, 0.15, 10, h=1.0, eps=0.0, maxit=1, p0=pbar)[0]
+    d = p1 - pbar
+    r = pr.Y - o.shoot(pr.X, pbar, o.GAUSS, 0.15, 10)[0]
+    errs = []
+    for t in (1e-3, 1e-4):
+        qa = o.shoot(pr.X, pbar + t * d, o.GAUSS, 0.15, 10)[0]
+        qb = o.shoot(pr.X, pbar - t * d, o.GAUSS, 0.15, 10)[0]
+        errs.append(np.abs((qa - qb) / (2 * t) - r).max() / np.abs(r).max())
+    assert errs[1] < 1e-7
+    assert errs[1] < 0.05 * errs[0]  # second order in t
