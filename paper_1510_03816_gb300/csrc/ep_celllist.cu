@@ -482,6 +482,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
                 const int h2 = h + dy * kHalo + dx;
                 const int len = c_len[h2], s0 = cst[h2];
                 const float sx = __fmul_rn((float)(-dx), e0), sy = __fmul_rn((float)(-dy), e1);
+#pragma unroll 2
                 for (int v = 0; v < len; ++v) {
                     const float4 rj = rec[s0 + v];
                     int jj = 0;
