@@ -283,3 +283,39 @@ def test_rules_no_update_and_converged_start(rule):
     # Y = X: converged before any update
     res = _match(pr.X, pr.X, prm, rule, h=1.0, eps=1e-12, maxit=5)
     assert res.status == ep.OK and res.iters == 0 and res.resid == 0.0
+
+
+# --------------------------------------------------------------------------- both sides of each solver switch
+
+
+def _grid(nx, ny, h, extra):
+    X = np.stack(np.meshgrid(np.arange(nx), np.arange(ny)), -1).reshape(-1, 2) * h + 0.2
+    return np.vstack([X, [[0.97, 0.97]]]) if extra else X  # one far point crosses the threshold
+
+
+@pytest.mark.parametrize("extra", [0, 1])
+def test_velocity_rule_at_the_factoring_threshold(extra):
+    # 512 landmarks: G(X) factored; 513: MINRES (tent sigma = 0.03 on a 0.025 grid)
+    X = _grid(32, 16, 0.025, extra)
+    Y = X + 0.002 * np.random.default_rng(11).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=0.03, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_VELOCITY, h=0.5, eps=0.0, maxit=1)
+    rp, st, it, r, hist = o.match_velocity(X, Y, ep.TENT, 0.03, 4, h=0.5, eps=0.0, maxit=1)
+    assert res.iters == it == 1
+    assert (res.products == 2) == (X.shape[0] <= 512)  # one solve per component when factored
+    assert rel(res.p0, rp) < 1e-9
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-9)
+
+
+@pytest.mark.parametrize("extra", [0, 1])
+def test_newton_rule_at_the_dense_threshold(extra):
+    # 192 landmarks (n dim = 384): dense Jacobian; 193 (386): Krylov (Gaussian sigma = 0.02, 0.04 grid)
+    X = _grid(16, 12, 0.04, extra)
+    Y = X + 0.002 * np.random.default_rng(12).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.02, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_NEWTON, h=1.0, eps=0.0, maxit=1)
+    rp, st, it, r, hist = o.match_newton(X, Y, ep.GAUSS, 0.02, 4, h=1.0, eps=0.0, maxit=1)
+    assert res.iters == it == 1
+    assert (res.products == X.size) == (X.size <= 384)  # the Jacobian's columns when dense
+    assert rel(res.p0, rp) < 1e-8
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-8)
