@@ -572,6 +572,20 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
 
             out[name]["cpu_baseline"] = _oracle_sample(
                 run_rule, "matchings/s", f"FP64 oracle {fn} (dense Jacobian or Gram matrix, LU solve), whole match")
+    # the Newton gain in mixed precision on the same workload: FP32 Jacobian (inexact Newton),
+    # FP64 residual, solve and update
+    prmm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    ep.match(Xc, Yc, prmm, h=1.0, eps=c.eps, maxit=c.maxit, rule=ep.RULE_NEWTON)
+    t0 = time.perf_counter()
+    r = ep.match(Xc, Yc, prmm, h=1.0, eps=c.eps, maxit=c.maxit, rule=ep.RULE_NEWTON)
+    dt = time.perf_counter() - t0
+    out["newton_mixed"] = {"workload": "circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, mixed precision, "
+                                       "h=1.0, Newton gain with an FP32 Jacobian",
+                           "seconds_per_match": dt, "matchings_per_s": 1.0 / dt, "iters": r.iters, "status": r.status,
+                           "resid": r.resid, "krylov_products": r.products,
+                           "roofline": {"bound": "latency", "note": f"{r.iters} updates, each a recorded mixed shoot, "
+                                        "one launch of 128 FP32 tangent shoots (one per CTA), an FP64 LU on one CTA; "
+                                        "the oracle's Newton time is the newton_fp64 row's"}}
     if with_cpu:
         def run_small(o):
             _, _, it, _, _ = o.match(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.0, eps=c.eps, maxit=c.maxit)

@@ -199,14 +199,14 @@ struct JacArgs {
 
 // Warp sum of V <= 8 doubles, reduce-scatter form; afterwards lane l holds the total
 // of value first(l) and the lanes with (l & (32 / P - 1)) == 0 hold distinct values.
-template <int V>
-__device__ __forceinline__ double warp_sum_scatter(double (&v)[V], int& first)
+template <int V, typename T>
+__device__ __forceinline__ T warp_sum_scatter(T (&v)[V], int& first)
 {
     constexpr int P = V == 1 ? 1 : V == 2 ? 2 : V <= 4 ? 4 : 8;
     const int lane = threadIdx.x & 31;
-    double u[P];
+    T u[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) u[k] = k < V ? v[k] : 0.0;
+    for (int k = 0; k < P; ++k) u[k] = k < V ? v[k] : T(0);
     first = 0;
     int cnt = P;
 #pragma unroll
@@ -217,8 +217,8 @@ __device__ __forceinline__ double warp_sum_scatter(double (&v)[V], int& first)
 #pragma unroll
             for (int k = 0; k < P / 2; ++k) {
                 if (k < h) {
-                    const double send = upper ? u[k] : u[k + h];
-                    const double keep = upper ? u[k + h] : u[k];
+                    const T send = upper ? u[k] : u[k + h];
+                    const T keep = upper ? u[k + h] : u[k];
                     u[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
                 }
             }
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jac_fp64(JacArgs a)
                     }
                 }
                 int first;
-                const double tot = warp_sum_scatter<S2>(h, first);
+                const double tot = warp_sum_scatter<S2, double>(h, first);
                 // the tangent RK4 stage of component `first` of row i, dk = (h_p, -h_q)
                 if ((lane & (32 / P - 1)) == 0 && first < S2) {
                     const int e = i * S2 + first;
@@ -320,6 +320,144 @@ __global__ void __launch_bounds__(kJacThreads) k_jac_fp64(JacArgs a)
     }
     // column c of D phi: the position part of the tangent at t1
     for (int r = threadIdx.x; r < N; r += kJacThreads) a.J[(size_t)c * N + r] = X0[(r / DIM) * S2 + (r % DIM)];
+}
+
+// FP32 kernel value, phi and psi (unscaled), for the mixed-precision Jacobian.
+template <int KER>
+__device__ __forceinline__ void kfun3_f32(float r2, float sigma, float& G, float& phi, float& psi)
+{
+    const float is = 1.0f / sigma;
+    if constexpr (KER == EP_GAUSS) {
+        G = expf(-0.5f * (r2 * (is * is)));
+        phi = -G * (is * is);
+        psi = G * (is * is) * (is * is);
+    } else if constexpr (KER == EP_TENT) {
+        const float r = sqrtf(r2);
+        const bool in = r < sigma && r2 > 0.0f;
+        const float rs = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        G = r < sigma ? 1.0f - r * is : 0.0f;
+        phi = in ? -is * rs : 0.0f;
+        psi = in ? is * rs * rs * rs : 0.0f;
+    } else {
+        const float r = sqrtf(r2);
+        const float rs = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        G = expf(-r * is);
+        phi = r2 > 0.0f ? -G * is * rs : 0.0f;
+        psi = r2 > 0.0f ? G * (is * is * rs * rs + is * rs * rs * rs) : 0.0f;
+    }
+}
+
+// The mixed-precision Jacobian: as k_jac_fp64 with FP32 pair terms and FP32 tangent
+// state, against the mixed shoot's recorded stages (scaled positions q' = s (q - c0)
+// and momenta in float4 records; d = (q'_i - q'_j) / s).  Newton converges with this
+// Jacobian as an inexact Newton method; the residual, the solve and the update stay FP64.
+struct JacMArgs {
+    int n, steps;
+    float dt, sigma, inv_s;
+    const float4* rec;  // (4 steps + 1) stage copies, (dim == 2 ? 1 : 2) float4 per particle
+    double* J;
+};
+
+template <int DIM>
+__device__ __forceinline__ void rec_load(const float4* Y, int i, float (&q)[DIM], float (&p)[DIM])
+{
+    if constexpr (DIM == 2) {
+        const float4 v = __ldg(Y + i);
+        q[0] = v.x; q[1] = v.y; p[0] = v.z; p[1] = v.w;
+    } else {
+        const float4 a = __ldg(Y + 2 * (size_t)i), b = __ldg(Y + 2 * (size_t)i + 1);
+        q[0] = a.x; q[1] = a.y; q[2] = a.z; p[0] = b.x; p[1] = b.y; p[2] = b.z;
+    }
+}
+
+template <int DIM, int KER>
+__global__ void __launch_bounds__(kJacThreads) k_jac_mixed(JacMArgs a)
+{
+    constexpr int S2 = 2 * DIM;
+    constexpr int P = S2 <= 4 ? 4 : 8;
+    constexpr int V = DIM == 2 ? 1 : 2;
+    extern __shared__ float jf[];
+    const int n = a.n;
+    const int N = n * DIM;
+    const int c = blockIdx.x;
+    const size_t sn = (size_t)S2 * n;
+    float* T0 = jf;
+    float* T1 = jf + sn;
+    float* X0 = jf + 2 * sn;
+    float* A = jf + 3 * sn;
+    for (int t = threadIdx.x; t < (int)sn; t += kJacThreads) {
+        const int i = t / S2, k = t % S2;
+        const float v = (k >= DIM && i * DIM + (k - DIM) == c) ? 1.0f : 0.0f;
+        T0[t] = v;
+        X0[t] = v;
+        A[t] = 0.0f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int W = kJacThreads / 32;
+    float* Tin = T0;
+    float* Tout = T1;
+    for (int k = 0; k < a.steps; ++k) {
+        for (int s = 0; s < 4; ++s) {
+            const float4* Y = a.rec + (size_t)(4 * k + s) * V * n;
+            for (int i = warp; i < n; i += W) {
+                float qi[DIM], pi[DIM], vqi[DIM], vpi[DIM];
+                rec_load<DIM>(Y, i, qi, pi);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    vqi[d] = Tin[i * S2 + d];
+                    vpi[d] = Tin[i * S2 + DIM + d];
+                }
+                float h[S2];
+#pragma unroll
+                for (int u = 0; u < S2; ++u) h[u] = 0.0f;
+                for (int j = lane; j < n; j += 32) {
+                    float qj[DIM], pj[DIM];
+                    rec_load<DIM>(Y, j, qj, pj);
+                    float dd[DIM], dv[DIM], vpj[DIM];
+                    float r2 = 0.0f, ddv = 0.0f, pp = 0.0f, a1 = 0.0f;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        dd[d] = (qi[d] - qj[d]) * a.inv_s;
+                        dv[d] = vqi[d] - Tin[j * S2 + d];
+                        vpj[d] = Tin[j * S2 + DIM + d];
+                        r2 += dd[d] * dd[d];
+                        ddv += dd[d] * dv[d];
+                        pp += pi[d] * pj[d];
+                        a1 += vpi[d] * pj[d] + pi[d] * vpj[d];
+                    }
+                    float G, phi, psi;
+                    kfun3_f32<KER>(r2, a.sigma, G, phi, psi);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) h[d] += G * vpj[d] + phi * ddv * pj[d];
+                    if (j != i) {
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d) h[DIM + d] += a1 * phi * dd[d] + pp * (phi * dv[d] + psi * ddv * dd[d]);
+                    }
+                }
+                int first;
+                const float tot = warp_sum_scatter<S2, float>(h, first);
+                if ((lane & (32 / P - 1)) == 0 && first < S2) {
+                    const int e = i * S2 + first;
+                    const float dk = first < DIM ? tot : -tot;
+                    if (s < 3) {
+                        const float cdt = (s == 2 ? 1.0f : 0.5f) * a.dt;
+                        Tout[e] = X0[e] + cdt * dk;
+                        A[e] = s == 0 ? dk : A[e] + 2.0f * dk;
+                    } else {
+                        const float nv = X0[e] + a.dt / 6.0f * (A[e] + dk);
+                        X0[e] = nv;
+                        Tout[e] = nv;
+                    }
+                }
+            }
+            __syncthreads();
+            float* tmp = Tin;
+            Tin = Tout;
+            Tout = tmp;
+        }
+    }
+    for (int r = threadIdx.x; r < N; r += kJacThreads) a.J[(size_t)c * N + r] = (double)X0[(r / DIM) * S2 + (r % DIM)];
 }
 
 // r = Y - Q(1) (Q(1): the first m entries of the step state) and the max-norm of r
@@ -432,7 +570,8 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restri
 // Device buffers of one tangent-linear problem.
 struct TanBufs {
     AllPairsBufs ap;
-    double* drec = nullptr;
+    double* drec = nullptr;  // FP64 recording
+    float4* rec = nullptr;   // mixed recording (scaled positions, FP32)
     double* dx = nullptr;
     double* dacc = nullptr;
     double* T[2] = {nullptr, nullptr};
@@ -442,23 +581,29 @@ struct TanBufs {
     int* err = nullptr;
 };
 
-size_t tan_bytes(int64_t n, int dim, int steps)
+size_t tan_bytes(int64_t n, int dim, int steps, int prec = EP_FP64)
 {
     Sizer z;
     const size_t m = (size_t)n * dim;
-    z.add(allpairs_bytes((int)n, dim, EP_FP64));
-    z.add(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));  // recorded stages
+    z.add(allpairs_bytes((int)n, dim, prec));
+    if (prec == EP_MIXED)
+        z.add(sizeof(float4) * (dim == 2 ? 1 : 2) * (size_t)n * (4 * (size_t)steps + 1));  // recorded stages
+    else
+        z.add(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));
     for (int k = 0; k < 4; ++k) z.add(sizeof(double) * 2 * m);  // dx, dacc, T[2]
     z.add(sizeof(double) * 2 * m * 2);                          // v0, out
     z.add(sizeof(unsigned) * 12);
     return z.total;
 }
 
-ep_status tan_carve(Arena* ar, int64_t n, int dim, int steps, TanBufs* t)
+ep_status tan_carve(Arena* ar, int64_t n, int dim, int steps, TanBufs* t, int prec = EP_FP64)
 {
     const size_t m = (size_t)n * dim;
-    EP_TRY(allpairs_carve(ar, (int)n, dim, EP_FP64, &t->ap));
-    t->drec = (double*)ar->carve(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));
+    EP_TRY(allpairs_carve(ar, (int)n, dim, prec, &t->ap));
+    if (prec == EP_MIXED)
+        t->rec = (float4*)ar->carve(sizeof(float4) * (dim == 2 ? 1 : 2) * (size_t)n * (4 * (size_t)steps + 1));
+    else
+        t->drec = (double*)ar->carve(sizeof(double) * 2 * m * (4 * (size_t)steps + 1));
     t->dx = (double*)ar->carve(sizeof(double) * 2 * m);
     t->dacc = (double*)ar->carve(sizeof(double) * 2 * m);
     t->T[0] = (double*)ar->carve(sizeof(double) * 2 * m);
@@ -471,11 +616,12 @@ ep_status tan_carve(Arena* ar, int64_t n, int dim, int steps, TanBufs* t)
     return EP_OK;
 }
 
-// Primal shoot from (q0, p0) with every stage input recorded in t.drec.
+// Primal shoot from (q0, p0) with every stage input recorded in t.drec (FP64) or
+// t.rec (mixed).
 ep_status tan_record(const ep_params& P, TanBufs& t, const double* q0, const double* p0, cudaStream_t st)
 {
     EP_TRY(allpairs_load(P, t.ap, q0, p0, st));
-    return allpairs_steps_rec(P, t.ap, P.steps, P.t1 / P.steps, nullptr, t.drec, st);
+    return allpairs_steps_rec(P, t.ap, P.steps, P.t1 / P.steps, t.rec, t.drec, st);
 }
 
 template <int DIM, int KER>
@@ -686,7 +832,11 @@ ep_status tangent_entry(const ep_params* params, int64_t n, const double* q0, co
 ep_status rule_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
                      ep_match_info* info, cudaStream_t st)
 {
-    if (P.precision != EP_FP64) return set_error("ep_match: the Newton gain runs in FP64"), EP_EINVAL;
+    const size_t m0 = (size_t)n * P.dim;
+    const bool mixed = P.precision == EP_MIXED;
+    if (mixed && m0 > (size_t)kDenseNewtonMax)
+        return set_error("ep_match: the mixed-precision Newton gain forms the whole Jacobian (n dim <= %d)",
+                         kDenseNewtonMax), EP_EINVAL;
     if (P.neigh == EP_CELLLIST) return set_error("ep_match: the Newton gain runs on the all-pairs path"), EP_EINVAL;
     if (P.inexact != 0.0) return set_error("ep_match: the Newton gain is built for the exact system"), EP_EINVAL;
     if (info->krylov < 0) return set_error("ep_match: krylov must be >= 0"), EP_EINVAL;
@@ -694,7 +844,7 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     // small problems form D phi whole (one CTA per column) and solve it densely
     const bool dense = m <= (size_t)kDenseNewtonMax;
     Sizer z;
-    z.add(tan_bytes(n, P.dim, P.steps));
+    z.add(tan_bytes(n, P.dim, P.steps, P.precision));
     z.add(sizeof(double) * m * 6);
     if (dense) {
         z.add(sizeof(double) * m * m);
@@ -704,7 +854,7 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     Arena* ar = nullptr;
     EP_TRY(arena_acquire(st, z.total, &ar));
     TanBufs t;
-    EP_TRY(tan_carve(ar, n, P.dim, P.steps, &t));
+    EP_TRY(tan_carve(ar, n, P.dim, P.steps, &t, P.precision));
     double* dX = (double*)ar->carve(sizeof(double) * m);
     double* dp = (double*)ar->carve(sizeof(double) * m);
     double* dk = (double*)ar->carve(sizeof(double) * m);
@@ -800,13 +950,30 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
             ja.sigma = P.sigma;
             ja.drec = t.drec;
             ja.J = dJ;
-            const size_t smem = sizeof(double) * 4 * 2 * (size_t)P.dim * n;
             ep_status ls = EP_EINVAL;
+            if (mixed) {
+                JacMArgs jm{};
+                jm.n = (int)n;
+                jm.steps = P.steps;
+                jm.dt = (float)(P.t1 / P.steps);
+                jm.sigma = (float)P.sigma;
+                jm.inv_s = (float)(1.0 / kernel_scale(P.kernel, P.sigma).s);
+                jm.rec = t.rec;
+                jm.J = dJ;
+                const size_t smem = sizeof(float) * 4 * 2 * (size_t)P.dim * n;
+#define EP_JAC_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) { count_launch(); k_jac_mixed<D, K><<<(unsigned)m, kJacThreads, smem, st>>>(jm); ls = EP_OK; }
+                EP_JAC_CASE(2, EP_GAUSS) EP_JAC_CASE(2, EP_TENT) EP_JAC_CASE(2, EP_EXPCONE)
+                EP_JAC_CASE(3, EP_GAUSS) EP_JAC_CASE(3, EP_TENT) EP_JAC_CASE(3, EP_EXPCONE)
+#undef EP_JAC_CASE
+            } else {
+                const size_t smem = sizeof(double) * 4 * 2 * (size_t)P.dim * n;
 #define EP_JAC_CASE(D, K) \
     if (P.dim == D && P.kernel == K) { count_launch(); k_jac_fp64<D, K><<<(unsigned)m, kJacThreads, smem, st>>>(ja); ls = EP_OK; }
-            EP_JAC_CASE(2, EP_GAUSS) EP_JAC_CASE(2, EP_TENT) EP_JAC_CASE(2, EP_EXPCONE)
-            EP_JAC_CASE(3, EP_GAUSS) EP_JAC_CASE(3, EP_TENT) EP_JAC_CASE(3, EP_EXPCONE)
+                EP_JAC_CASE(2, EP_GAUSS) EP_JAC_CASE(2, EP_TENT) EP_JAC_CASE(2, EP_EXPCONE)
+                EP_JAC_CASE(3, EP_GAUSS) EP_JAC_CASE(3, EP_TENT) EP_JAC_CASE(3, EP_EXPCONE)
 #undef EP_JAC_CASE
+            }
             if (ls != EP_OK) return set_error("ep_match: no Jacobian kernel for this kernel"), ls;
             EP_TRY_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int), st));
             count_launch(2);

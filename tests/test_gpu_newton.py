@@ -161,11 +161,13 @@ def test_velocity_rule_ragged_rows_2d():
 def test_rule_refusals():
     X, _ = cloud(20, 2, seed=97)
     Y = X + 0.01
-    for prec in (ep.MIXED,):
-        prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=prec, neigh=ep.ALLPAIRS)
-        for rule in (ep.RULE_NEWTON, ep.RULE_VELOCITY):
-            with pytest.raises(ep.EPError):
-                _match(X, Y, prm, rule, maxit=3)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    with pytest.raises(ep.EPError):
+        _match(X, Y, prm, ep.RULE_VELOCITY, maxit=3)
+    # the mixed-precision Newton gain forms the whole Jacobian: n dim <= 384 only
+    Xb, _ = cloud(200, 2, seed=96)
+    with pytest.raises(ep.EPError):
+        _match(Xb, Xb + 0.01, prm, ep.RULE_NEWTON, maxit=3)
     prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS, inexact=0.1)
     with pytest.raises(ep.EPError):
         _match(X, Y, prm, ep.RULE_NEWTON, maxit=3)
@@ -319,3 +321,35 @@ def test_newton_rule_at_the_dense_threshold(extra):
     assert (res.products == X.size) == (X.size <= 384)  # the Jacobian's columns when dense
     assert rel(res.p0, rp) < 1e-8
     np.testing.assert_allclose(res.hist, hist, rtol=1e-8)
+
+
+# --------------------------------------------------------------------------- mixed precision (Newton)
+
+
+@pytest.mark.parametrize("kernel,sigma,n,h", [(ep.GAUSS, 0.1, 12, 1.0), (ep.TENT, 0.45, 16, 0.8),
+                                              (ep.EXPCONE, 0.3, 16, 0.8)])
+def test_newton_rule_mixed_precision(kernel, sigma, n, h):
+    # FP32 Jacobian (an inexact Newton method), FP64 residual, solve and update: the
+    # iteration converges to the mixed shooting map's root, which agrees with the FP64
+    # oracle's to the mixed-precision bound.  The mixed shoot's endpoint carries FP32
+    # rounding noise of ~1e-8 (the residual cannot fall below it), so eps = 1e-7.
+    pr = w.circle_to_ellipse(n, sigma=sigma, kernel=kernel, steps=12)
+    prm = ep.params(dim=2, kernel=kernel, sigma=sigma, steps=12, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    res = _match(pr.X, pr.Y, prm, ep.RULE_NEWTON, h=h, eps=1e-7, maxit=40)
+    rp, st, it, r, hist = o.match_newton(pr.X, pr.Y, kernel, sigma, 12, h=h, eps=1e-7, maxit=40)
+    assert res.status == st == ep.OK
+    assert it <= res.iters <= it + 3
+    assert rel(res.p0, rp) < 1e-4
+    assert res.products == res.iters * pr.X.size
+    # early iterates follow the exact Newton iteration closely
+    np.testing.assert_allclose(res.hist[:2], hist[:2], rtol=1e-4)
+
+
+def test_newton_rule_mixed_3d():
+    X, _ = cloud(30, 3, seed=93)
+    Y = X + 0.01 * np.random.default_rng(94).normal(size=X.shape)
+    prm = ep.params(dim=3, kernel=ep.GAUSS, sigma=0.15, steps=6, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_NEWTON, h=1.0, eps=1e-7, maxit=20)
+    rp, st, it, r, hist = o.match_newton(X, Y, ep.GAUSS, 0.15, 6, h=1.0, eps=1e-7, maxit=20)
+    assert res.status == st == ep.OK and it <= res.iters <= it + 3
+    assert rel(res.p0, rp) < 1e-4
