@@ -353,3 +353,44 @@ def test_newton_rule_mixed_3d():
     rp, st, it, r, hist = o.match_newton(X, Y, ep.GAUSS, 0.15, 6, h=1.0, eps=1e-7, maxit=20)
     assert res.status == st == ep.OK and it <= res.iters <= it + 3
     assert rel(res.p0, rp) < 1e-4
+
+
+# --------------------------------------------------------------------------- the C ABI: host arrays, device history, initial guess
+
+
+@pytest.mark.parametrize("rule", [ep.RULE_NEWTON, ep.RULE_VELOCITY])
+def test_rules_host_arrays_and_initial_guess(rule):
+    pr = w.circle_to_ellipse(12, sigma=0.1, kernel=ep.GAUSS, steps=10)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    h = 1.0 if rule == ep.RULE_NEWTON else 0.5
+    f = o.match_newton if rule == ep.RULE_NEWTON else o.match_velocity
+    # numpy in, numpy out
+    res = ep.match(pr.X, pr.Y, prm, h=h, eps=0.0, maxit=2, rule=rule)
+    assert isinstance(res.p0, np.ndarray)
+    rp = f(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=h, eps=0.0, maxit=2)[0]
+    assert rel(res.p0, rp) < 1e-9
+    # a non-zero initial guess: two more updates from there equal four from zero
+    res2 = ep.match(pr.X, pr.Y, prm, h=h, eps=0.0, maxit=2, rule=rule, p0=res.p0)
+    rp4 = f(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=h, eps=0.0, maxit=4)[0]
+    assert rel(res2.p0, rp4) < 1e-8
+
+
+@pytest.mark.parametrize("rule", [ep.RULE_NEWTON, ep.RULE_VELOCITY])
+def test_rules_history_in_device_memory(rule):
+    import ctypes
+    pr = w.circle_to_ellipse(12, sigma=0.1, kernel=ep.GAUSS, steps=10)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    X, Y = cuda(pr.X), cuda(pr.Y)
+    p = torch.zeros_like(X)
+    hist = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    info = ep.MatchInfo(0.5, 0.0, 3, 0, 0.0, 0.0, hist.data_ptr(), int(rule), 0)
+    lib = ep.load()
+    st = lib.ep_match(ctypes.byref(ep._with_dim(prm, 2)), 12, X.data_ptr(), Y.data_ptr(), p.data_ptr(),
+                      ctypes.byref(info), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st == ep.ENOTCONVERGED and info.iters == 3
+    f = o.match_newton if rule == ep.RULE_NEWTON else o.match_velocity
+    rp, _, _, _, rh = f(pr.X, pr.Y, o.GAUSS, 0.1, 10, h=0.5, eps=0.0, maxit=3)
+    np.testing.assert_allclose(hist.cpu().numpy(), rh, rtol=1e-9)
+    assert rel(p, rp) < 1e-9
+    assert info.resid_inf == pytest.approx(rh[-1], rel=1e-9)
