@@ -586,6 +586,18 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
                            "roofline": {"bound": "latency", "note": f"{r.iters} updates, each a recorded mixed shoot, "
                                         "one launch of 128 FP32 tangent shoots (one per CTA), an FP64 LU on one CTA; "
                                         "the oracle's Newton time is the newton_fp64 row's"}}
+    # the velocity update in mixed precision on the same workload: mixed shoots, G(X) factored once
+    ep.match(Xc, Yc, prmm, h=0.5, eps=c.eps, maxit=c.maxit, rule=ep.RULE_VELOCITY)
+    t0 = time.perf_counter()
+    r = ep.match(Xc, Yc, prmm, h=0.5, eps=c.eps, maxit=c.maxit, rule=ep.RULE_VELOCITY)
+    dt = time.perf_counter() - t0
+    out["velocity_mixed"] = {"workload": "circle_to_ellipse N=64, tent sigma=0.25, 50 steps, eps 1e-6, mixed precision, "
+                                         "h=0.5, velocity update h G(X)^-1 r",
+                             "seconds_per_match": dt, "matchings_per_s": 1.0 / dt, "iters": r.iters, "status": r.status,
+                             "resid": r.resid, "krylov_products": r.products,
+                             "roofline": {"bound": "latency", "note": f"{r.iters} updates, each a mixed persistent shoot, "
+                                          "an FP64 residual and one warp's substitutions with the factored G(X); "
+                                          "the oracle's time is the velocity_fp64 row's"}}
     if with_cpu:
         def run_small(o):
             _, _, it, _, _ = o.match(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.0, eps=c.eps, maxit=c.maxit)

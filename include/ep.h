@@ -62,9 +62,9 @@ typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
  *  EP_RULE_NEWTON    p0 += h (D phi)^-1 r      the gain M = h (D phi)^-1 of Theorem 1,
  *                                              D phi = dQ(1)/dp0 of the RK4 shoot
  * Both solved rules run on the all-pairs path of the exact system (EP_EINVAL
- * otherwise); the velocity rule in FP64, the Newton rule in FP64 or, for
- * n dim <= 384, in mixed precision (an FP32 Jacobian, i.e. inexact Newton, with the
- * FP64 residual, solve and update).
+ * otherwise), in FP64 or in mixed precision: the velocity rule for n <= 512 (mixed
+ * shoots, G(X) in FP64 factored once), the Newton rule for n dim <= 384 (an FP32
+ * Jacobian, i.e. inexact Newton); the residual, solve and update are FP64.
  * The velocity rule runs inside the device-resident matching launch: for n <= 512
  * it factors G(X) once (LU with partial pivoting) and solves each update with the
  * factors; otherwise (or when a pivot vanishes) MINRES on the symmetric G(X) (the

@@ -516,9 +516,10 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     const bool device_loop = P.precision == EP_FP64 && !use_celllist(P, n) &&
                              ((info->rule == EP_RULE_MOMENTUM && n <= kDeviceMatchMaxN) ||
                               (info->rule == EP_RULE_VELOCITY && P.inexact == 0.0));
+    // the velocity update in mixed precision: mixed shoots, G(X) factored once in FP64
+    if (info->rule == EP_RULE_VELOCITY && P.precision == EP_MIXED) return velocity_mixed_match(P, n, X, Y, p0, info, st);
     if (info->rule == EP_RULE_VELOCITY && !device_loop)
-        return set_error("ep_match: the velocity update runs in FP64 on the all-pairs path of the exact system"),
-               EP_EINVAL;
+        return set_error("ep_match: the velocity update runs on the all-pairs path of the exact system"), EP_EINVAL;
     // the Newton gain: host GMRES over tangent-linear shoots on the device
     if (info->rule == EP_RULE_NEWTON) return rule_match(P, n, X, Y, p0, info, st);
     // small 2-D mixed problems: the whole feedback loop on one CTA (no grid-wide sync per stage)

@@ -54,6 +54,8 @@ ep_status tangent_entry(const ep_params* params, int64_t n, const double* q0, co
                         const double* vp0, double* q1, double* p1, double* vq1, double* vp1, void* stream);
 ep_status rule_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
                      ep_match_info* info, cudaStream_t st);
+ep_status velocity_mixed_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
+                               ep_match_info* info, cudaStream_t st);
 constexpr int64_t kSmallMatchMaxN = 384;
 
 }  // namespace ep

@@ -567,6 +567,47 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restri
     }
 }
 
+// ------------------------------------------------------------------ velocity update, mixed precision
+// G(X) (FP64 kernel values, all n^2 entries, row-major = column-major: symmetric).
+template <int DIM, int KER>
+__global__ void k_gram_fp64(const double* __restrict__ X, int n, double sigma, double* __restrict__ Gm)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * n) return;
+    const int i = (int)(e / n), j = (int)(e % n);
+    double r2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        const double d = X[(size_t)i * DIM + c] - X[(size_t)j * DIM + c];
+        r2 += d * d;
+    }
+    double G, phi;
+    kfun_f64<KER>(r2, sigma, G, phi);
+    Gm[e] = G;
+}
+
+// LU factors of G(X) in place (one CTA); *ok = 1 on success.
+__global__ void __launch_bounds__(kLuThreads) k_lu_factor(int n, double* Gm, int* piv, int* ok)
+{
+    __shared__ double s_v[kLuThreads / 32 + 1];
+    __shared__ int s_i[kLuThreads / 32 + 1];
+    const bool good = cta_lu_factor<kLuThreads>(n, Gm, piv, s_v, s_i);
+    if (threadIdx.x == 0) *ok = good ? 1 : 0;
+}
+
+// delta = G(X)^-1 r per component (one warp; scratch: n doubles), r and delta (n, dim).
+__global__ void k_gram_solve(int n, int dim, const double* Gm, const int* piv, const double* __restrict__ r,
+                             double* __restrict__ delta, double* scratch)
+{
+    for (int c = 0; c < dim; ++c) {
+        for (int i = threadIdx.x; i < n; i += 32) scratch[i] = r[(size_t)i * dim + c];
+        __syncwarp();
+        warp_lu_solve(n, Gm, piv, scratch);
+        for (int i = threadIdx.x; i < n; i += 32) delta[(size_t)i * dim + c] = scratch[i];
+        __syncwarp();
+    }
+}
+
 // Device buffers of one tangent-linear problem.
 struct TanBufs {
     AllPairsBufs ap;
@@ -1016,6 +1057,115 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
     info->H = H;
     if (status == EP_ENOTCONVERGED) set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", k, res, info->eps);
     if (status == EP_EDIVERGED && !singular) set_error("ep_match: residual became non-finite after %d updates", k);
+    return status;
+}
+
+// Algorithm 1 with the velocity update in mixed precision (n <= kGramLuMaxMixed):
+// mixed shoots, FP64 residual, G(X) built in FP64 and factored once, each update a
+// forward and a back substitution per component, FP64 update.
+constexpr int64_t kGramLuMaxMixed = 512;
+
+ep_status velocity_mixed_match(const ep_params& P, int64_t n, const double* X, const double* Y, double* p0,
+                               ep_match_info* info, cudaStream_t st)
+{
+    if (n > kGramLuMaxMixed)
+        return set_error("ep_match: the mixed-precision velocity update factors G(X) (n <= %lld)",
+                         (long long)kGramLuMaxMixed), EP_EINVAL;
+    if (P.neigh == EP_CELLLIST) return set_error("ep_match: the velocity update runs on the all-pairs path"), EP_EINVAL;
+    if (P.inexact != 0.0) return set_error("ep_match: the velocity update is built for the exact system"), EP_EINVAL;
+    const size_t m = (size_t)n * P.dim;
+    Sizer z;
+    z.add(allpairs_bytes((int)n, P.dim, EP_MIXED));
+    z.add(sizeof(double) * (size_t)n * n);
+    z.add(sizeof(int) * (size_t)n);
+    for (int k = 0; k < 7; ++k) z.add(sizeof(double) * m);
+    z.add(64);
+    Arena* ar = nullptr;
+    EP_TRY(arena_acquire(st, z.total, &ar));
+    AllPairsBufs ap;
+    EP_TRY(allpairs_carve(ar, (int)n, P.dim, EP_MIXED, &ap));
+    double* Gm = (double*)ar->carve(sizeof(double) * (size_t)n * n);
+    int* piv = (int*)ar->carve(sizeof(int) * (size_t)n);
+    double* dX = (double*)ar->carve(sizeof(double) * m);
+    double* dY = (double*)ar->carve(sizeof(double) * m);
+    double* dp = (double*)ar->carve(sizeof(double) * m);
+    double* dr = (double*)ar->carve(sizeof(double) * m);
+    double* dl = (double*)ar->carve(sizeof(double) * m);
+    double* dk = (double*)ar->carve(sizeof(double) * m);
+    double* dd = (double*)ar->carve(sizeof(double) * m);
+    unsigned long long* dres = (unsigned long long*)ar->carve(64);
+    if (!dres) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+    int* dok = (int*)(dres + 4);
+    EP_TRY(copy_in(dX, X, m, st));
+    EP_TRY(copy_in(dY, Y, m, st));
+    EP_TRY(copy_in(dp, p0, m, st));
+    const double h = info->h > 0.0 ? info->h : 1.0;
+    info->h = h;
+    const bool hist_dev = info->hist && dev_ptr(info->hist);
+    // G(X) and its LU factors, once
+    const long long nn = (long long)n * n;
+    ep_status ls = EP_EINVAL;
+#define EP_GRAM_CASE(D, K) \
+    if (P.dim == D && P.kernel == K) { count_launch(); k_gram_fp64<D, K><<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(dX, (int)n, P.sigma, Gm); ls = EP_OK; }
+    EP_GRAM_CASE(2, EP_GAUSS) EP_GRAM_CASE(2, EP_TENT) EP_GRAM_CASE(2, EP_EXPCONE)
+    EP_GRAM_CASE(3, EP_GAUSS) EP_GRAM_CASE(3, EP_TENT) EP_GRAM_CASE(3, EP_EXPCONE)
+#undef EP_GRAM_CASE
+    if (ls != EP_OK) return set_error("ep_match: no Gram kernel for this kernel"), ls;
+    count_launch();
+    k_lu_factor<<<1, kLuThreads, 0, st>>>((int)n, Gm, piv, dok);
+    EP_TRY_CUDA(cudaGetLastError());
+    int ok = 0;
+    EP_TRY_CUDA(cudaMemcpyAsync(&ok, dok, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (!ok) return set_error("ep_match: G(X) is singular (the velocity update needs G(X)^-1)"), EP_EDIVERGED;
+    ep_status status = EP_ENOTCONVERGED;
+    int k = 0;
+    double res = 0.0;
+    const double dt = P.t1 / P.steps;
+    for (;;) {
+        EP_TRY(allpairs_load(P, ap, dX, dp, st));
+        EP_TRY(allpairs_steps(P, ap, P.steps, dt, st));
+        unsigned long long rb = 0;
+        EP_TRY_CUDA(cudaMemsetAsync(dres, 0, sizeof(unsigned long long), st));
+        count_launch();
+        k_residual<<<(unsigned)std::min<size_t>((m + 255) / 256, 1024), 256, 0, st>>>(dY, ap.x, (int)m, dr, dres);
+        EP_TRY_CUDA(cudaGetLastError());
+        EP_TRY_CUDA(cudaMemcpyAsync(&rb, dres, sizeof rb, cudaMemcpyDeviceToHost, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+        const bool finite = rb < 0x7FF0000000000000ull;
+        memcpy(&res, &rb, sizeof res);
+        if (!finite) res = NAN;
+        if (info->hist) {
+            if (hist_dev)
+                EP_TRY_CUDA(cudaMemcpyAsync(info->hist + k, &res, sizeof(double), cudaMemcpyHostToDevice, st));
+            else
+                info->hist[k] = res;
+        }
+        if (!finite) { status = EP_EDIVERGED; break; }
+        if (res < info->eps) { status = EP_OK; break; }
+        if (k == info->maxit) { status = EP_ENOTCONVERGED; break; }
+        count_launch(2);
+        k_gram_solve<<<1, 32, 0, st>>>((int)n, P.dim, Gm, piv, dr, dl, dk);
+        k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dl, h, (int)m);
+        EP_TRY_CUDA(cudaGetLastError());
+        info->products += P.dim;
+        ++k;
+    }
+    info->iters = k;
+    info->resid_inf = res;
+    EP_TRY_CUDA(cudaMemcpyAsync(p0, dp, sizeof(double) * m, cudaMemcpyDefault, st));
+    // H(X, p0) of Eq. H: 1/2 sum_i p_i . dq_i
+    EP_TRY(allpairs_load(P, ap, dX, dp, st));
+    EP_TRY(allpairs_rhs(P, ap, dk, dd, st));
+    std::vector<double> hp(m), hdq(m);
+    EP_TRY_CUDA(cudaMemcpyAsync(hp.data(), dp, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(hdq.data(), dk, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    double H = 0.0;
+    for (size_t a = 0; a < m; ++a) H += 0.5 * hp[a] * hdq[a];
+    info->H = H;
+    if (status == EP_ENOTCONVERGED) set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", k, res, info->eps);
+    if (status == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", k);
     return status;
 }
 

@@ -162,12 +162,14 @@ def test_rule_refusals():
     X, _ = cloud(20, 2, seed=97)
     Y = X + 0.01
     prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.MIXED, neigh=ep.ALLPAIRS)
-    with pytest.raises(ep.EPError):
-        _match(X, Y, prm, ep.RULE_VELOCITY, maxit=3)
-    # the mixed-precision Newton gain forms the whole Jacobian: n dim <= 384 only
+    # the mixed-precision Newton gain forms the whole Jacobian (n dim <= 384), the mixed
+    # velocity update factors G(X) (n <= 512)
     Xb, _ = cloud(200, 2, seed=96)
     with pytest.raises(ep.EPError):
         _match(Xb, Xb + 0.01, prm, ep.RULE_NEWTON, maxit=3)
+    Xc = np.random.default_rng(95).uniform(0, 1, size=(600, 2))
+    with pytest.raises(ep.EPError):
+        _match(Xc, Xc + 0.01, prm, ep.RULE_VELOCITY, maxit=3)
     prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.2, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS, inexact=0.1)
     with pytest.raises(ep.EPError):
         _match(X, Y, prm, ep.RULE_NEWTON, maxit=3)
@@ -394,3 +396,32 @@ def test_rules_history_in_device_memory(rule):
     np.testing.assert_allclose(hist.cpu().numpy(), rh, rtol=1e-9)
     assert rel(p, rp) < 1e-9
     assert info.resid_inf == pytest.approx(rh[-1], rel=1e-9)
+
+
+# --------------------------------------------------------------------------- mixed precision (velocity update)
+
+
+@pytest.mark.parametrize("kernel,sigma,h", [(ep.TENT, 0.45, 0.5), (ep.EXPCONE, 0.3, 0.7), (ep.GAUSS, 0.12, 0.6)])
+def test_velocity_rule_mixed_precision(kernel, sigma, h):
+    # mixed shoots, G(X) in FP64 factored once: the iterates follow the FP64 oracle's to the
+    # mixed-precision bound (eps above the mixed shoot's ~1e-8 endpoint noise)
+    pr = w.circle_to_ellipse(16, sigma=sigma, kernel=kernel, steps=20)
+    prm = ep.params(dim=2, kernel=kernel, sigma=sigma, steps=20, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    res = _match(pr.X, pr.Y, prm, ep.RULE_VELOCITY, h=h, eps=1e-7, maxit=100)
+    rp, st, it, r, hist = o.match_velocity(pr.X, pr.Y, kernel, sigma, 20, h=h, eps=1e-7, maxit=100)
+    assert res.status == st == ep.OK
+    assert abs(res.iters - it) <= 1
+    k = min(len(res.hist), len(hist))
+    # residuals differ by the mixed shoot's endpoint error (~2e-8 here; the mixed bound is
+    # 1e-4 of the positions)
+    np.testing.assert_allclose(res.hist[:k], hist[:k], rtol=1e-4, atol=1e-6)
+    assert rel(res.p0, rp) < 1e-4
+
+
+def test_velocity_rule_mixed_bench_workload():
+    c = w.circle_to_ellipse()
+    prm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    res = _match(c.X, c.Y, prm, ep.RULE_VELOCITY, h=0.5, eps=c.eps, maxit=c.maxit)
+    rp, st, it, r, hist = o.match_velocity(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.5, eps=c.eps, maxit=c.maxit)
+    assert res.status == st == ep.OK and abs(res.iters - it) <= 1
+    assert rel(res.p0, rp) < 1e-4
