@@ -54,26 +54,26 @@ typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
 /* EP_AUTO picks the cell list for EP_TENT when it pays off, else all-pairs. */
 typedef enum { EP_AUTO = 0, EP_ALLPAIRS = 1, EP_CELLLIST = 2 } ep_neigh;
 
-/* Update rule of ep_match (Algorithm 1 step 3-4 and Sec. 5), r = Y - Q(1):
- *  EP_RULE_MOMENTUM  p0 += h r                 M = h I applied to the momenta (default)
- *  EP_RULE_VELOCITY  p0 += h G(X)^-1 r         the velocity u = G(X) p0 (Eq. u at t = 0)
- *                                              is updated by u += h r and p0 recovered
- *                                              from u (Algorithm 1 step 4)
- *  EP_RULE_NEWTON    p0 += h (D phi)^-1 r      the gain M = h (D phi)^-1 of Theorem 1,
- *                                              D phi = dQ(1)/dp0 of the RK4 shoot
- * Both solved rules run on the all-pairs path of the exact system (EP_EINVAL
- * otherwise), in FP64 or in mixed precision: the velocity rule for n <= 512 (mixed
- * shoots, G(X) in FP64 factored once), the Newton rule for n dim <= 384 (an FP32
- * Jacobian, i.e. inexact Newton); the residual, solve and update are FP64.
- * The velocity rule runs inside the device-resident matching launch: for n <= 512
- * it factors G(X) once (LU with partial pivoting) and solves each update with the
- * factors; otherwise (or when a pivot vanishes) MINRES on the symmetric G(X) (the
- * tent's need not be positive definite), one all-pairs Gram product per iteration.  The Newton rule forms D phi whole on the device (one
- * tangent-linear shoot per column, all in one launch) and solves it by Gaussian
- * elimination with partial pivoting when n dim <= 384 (a singular D phi returns
- * EP_EDIVERGED); larger problems run restarted GMRES on the host
- * (ep_match_info.krylov vectors) whose products are tangent-linear shoots along
- * (0, v) on the device (ep_shoot_tangent). */
+/* Update rule of ep_match (Algorithm 1 steps 3-4 and Sec. 5), r = Y - Q(1):
+ *  EP_RULE_MOMENTUM  p0 += h r              M = h I applied to the momenta (default)
+ *  EP_RULE_VELOCITY  p0 += h G(X)^-1 r      the velocity u = G(X) p0 (Eq. u at t = 0) is
+ *                                           updated by u += h r and p0 recovered from u
+ *                                           (Algorithm 1 step 4)
+ *  EP_RULE_NEWTON    p0 += h (D phi)^-1 r   the gain M = h (D phi)^-1 of Theorem 1,
+ *                                           D phi = dQ(1)/dp0 of the RK4 shoot
+ * The solved rules (velocity, Newton) run on the all-pairs path of the exact system
+ * (EP_EINVAL otherwise); their residual, solve and update are FP64.
+ *  - Velocity, FP64: inside the device-resident matching launch.  For n <= 512 G(X)
+ *    is factored once (LU with partial pivoting); otherwise, or when a pivot
+ *    vanishes, every update runs MINRES on the symmetric G(X) (the tent's need not
+ *    be positive definite), one all-pairs Gram product per iteration.
+ *  - Velocity, mixed precision (n <= 512): mixed shoots, G(X) in FP64 factored once.
+ *  - Newton, n dim <= 384: D phi formed whole on the device, one tangent-linear shoot
+ *    per column, all in one launch (FP64; FP32 in mixed precision, an inexact
+ *    Newton method), solved by Gaussian elimination with partial pivoting (a
+ *    singular D phi returns EP_EDIVERGED).
+ *  - Newton, FP64, larger: restarted GMRES on the host (ep_match_info.krylov vectors)
+ *    whose products are tangent-linear shoots along (0, v) (ep_shoot_tangent). */
 typedef enum { EP_RULE_MOMENTUM = 0, EP_RULE_VELOCITY = 1, EP_RULE_NEWTON = 2 } ep_rule;
 
 typedef struct {
