@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--profile-rk4-steps", type=int, default=0,
                     help="with --profile: RK4 steps per shoot (0 = the workload's 100), for short captures")
     ap.add_argument("--profile-row", default="", choices=["", "cell_list", "batched", "tangent", "match_fp64",
-                                                           "velocity", "adjoint"],
+                                                           "velocity", "adjoint", "newton", "newton_mixed"],
                     help="run one small case of that secondary row (for ncu captures); no JSON line")
     return ap.parse_args()
 
@@ -87,13 +87,21 @@ def profile_row(name: str) -> None:
     tangent    the N = 1024 Fourier-curve tangent shoot, FP64, 5 steps (k_tangent_fp64)
     match_fp64 the N = 64 circle -> ellipse FP64 match, 5 updates (k_match_fp64)
     velocity   the same with the velocity update, 3 updates (factored G(X) inside k_match_fp64)
-    adjoint    one gradient of the N = 16384 3-D star-surface workload (100 steps, checkpoints every 10)"""
+    adjoint    one gradient of the N = 16384 3-D star-surface workload (100 steps, checkpoints every 10)
+    newton     the N = 64 circle -> ellipse Newton matching, FP64, 1 update (k_jac_fp64, k_lu_solve)
+    newton_mixed  the same in mixed precision (k_jac_mixed)"""
     import torch
     from paper_1510_03816_gb300 import ep, workloads
 
     ep.load()
     dev = "cuda"
-    if name == "adjoint":
+    if name in ("newton", "newton_mixed"):
+        c = workloads.circle_to_ellipse()
+        prec = ep.FP64 if name == "newton" else ep.MIXED
+        prm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=prec, neigh=ep.ALLPAIRS)
+        ep.match(torch.tensor(c.X, device=dev), torch.tensor(c.Y, device=dev), prm, h=1.0, eps=0.0, maxit=1,
+                 rule=ep.RULE_NEWTON)
+    elif name == "adjoint":
         a3 = workloads.star_surface_3d()
         X3, Y3, p3 = (torch.tensor(v, device=dev) for v in (a3.X, a3.Y, a3.p0))
         prm3 = ep.params(dim=3, kernel=ep.GAUSS, sigma=a3.sigma, steps=a3.steps, precision=ep.MIXED)

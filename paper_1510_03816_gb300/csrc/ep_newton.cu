@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_fp64(TanArgs a)
 // once.  One CTA then solves (D phi) delta = r by Gaussian elimination with
 // partial pivoting.
 constexpr int kDenseNewtonMax = 384;
-constexpr int kJacThreads = 256;
+constexpr int kJacThreads = 256;       // FP64 columns: the FP64 pipe is the bound
+constexpr int kJacMixedThreads = 512;  // FP32 columns: latency-bound, more warps per column
 
 struct JacArgs {
     int n, steps;
@@ -371,7 +372,7 @@ __device__ __forceinline__ void rec_load(const float4* Y, int i, float (&q)[DIM]
 }
 
 template <int DIM, int KER>
-__global__ void __launch_bounds__(kJacThreads) k_jac_mixed(JacMArgs a)
+__global__ void __launch_bounds__(kJacMixedThreads) k_jac_mixed(JacMArgs a)
 {
     constexpr int S2 = 2 * DIM;
     constexpr int P = S2 <= 4 ? 4 : 8;
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jac_mixed(JacMArgs a)
     float* T1 = jf + sn;
     float* X0 = jf + 2 * sn;
     float* A = jf + 3 * sn;
-    for (int t = threadIdx.x; t < (int)sn; t += kJacThreads) {
+    for (int t = threadIdx.x; t < (int)sn; t += kJacMixedThreads) {
         const int i = t / S2, k = t % S2;
         const float v = (k >= DIM && i * DIM + (k - DIM) == c) ? 1.0f : 0.0f;
         T0[t] = v;
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jac_mixed(JacMArgs a)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int W = kJacThreads / 32;
+    constexpr int W = kJacMixedThreads / 32;
     float* Tin = T0;
     float* Tout = T1;
     for (int k = 0; k < a.steps; ++k) {
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jac_mixed(JacMArgs a)
             Tout = tmp;
         }
     }
-    for (int r = threadIdx.x; r < N; r += kJacThreads) a.J[(size_t)c * N + r] = (double)X0[(r / DIM) * S2 + (r % DIM)];
+    for (int r = threadIdx.x; r < N; r += kJacMixedThreads) a.J[(size_t)c * N + r] = (double)X0[(r / DIM) * S2 + (r % DIM)];
 }
 
 // r = Y - Q(1) (Q(1): the first m entries of the step state) and the max-norm of r
@@ -1003,7 +1004,7 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
                 jm.J = dJ;
                 const size_t smem = sizeof(float) * 4 * 2 * (size_t)P.dim * n;
 #define EP_JAC_CASE(D, K) \
-    if (P.dim == D && P.kernel == K) { count_launch(); k_jac_mixed<D, K><<<(unsigned)m, kJacThreads, smem, st>>>(jm); ls = EP_OK; }
+    if (P.dim == D && P.kernel == K) { count_launch(); k_jac_mixed<D, K><<<(unsigned)m, kJacMixedThreads, smem, st>>>(jm); ls = EP_OK; }
                 EP_JAC_CASE(2, EP_GAUSS) EP_JAC_CASE(2, EP_TENT) EP_JAC_CASE(2, EP_EXPCONE)
                 EP_JAC_CASE(3, EP_GAUSS) EP_JAC_CASE(3, EP_TENT) EP_JAC_CASE(3, EP_EXPCONE)
 #undef EP_JAC_CASE
