@@ -512,7 +512,7 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
         return EP_OK;
     }
     // the plain FP64 all-pairs method runs the whole feedback loop on the device, with
-    // the momentum rule or the velocity rule (in-kernel MINRES)
+    // the momentum rule or the velocity rule (G(X) factored in the launch, or MINRES)
     const bool device_loop = P.precision == EP_FP64 && !use_celllist(P, n) &&
                              ((info->rule == EP_RULE_MOMENTUM && n <= kDeviceMatchMaxN) ||
                               (info->rule == EP_RULE_VELOCITY && P.inexact == 0.0));
@@ -520,7 +520,8 @@ ep_status ep_match(const ep_params* params, int64_t n, const double* X, const do
     if (info->rule == EP_RULE_VELOCITY && P.precision == EP_MIXED) return velocity_mixed_match(P, n, X, Y, p0, info, st);
     if (info->rule == EP_RULE_VELOCITY && !device_loop)
         return set_error("ep_match: the velocity update runs on the all-pairs path of the exact system"), EP_EINVAL;
-    // the Newton gain: host GMRES over tangent-linear shoots on the device
+    // the Newton gain: the whole Jacobian and a dense solve for small problems, host
+    // GMRES over tangent-linear shoots beyond (ep_newton.cu)
     if (info->rule == EP_RULE_NEWTON) return rule_match(P, n, X, Y, p0, info, st);
     // small 2-D mixed problems: the whole feedback loop on one CTA (no grid-wide sync per stage)
     if (P.precision == EP_MIXED && P.dim == 2 && !use_celllist(P, n) && n <= kSmallMatchMaxN && P.inexact == 0.0) {
