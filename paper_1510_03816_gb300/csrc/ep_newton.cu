@@ -489,14 +489,28 @@ __global__ void k_axpy_update(double* __restrict__ p, const double* __restrict__
 // Solve J x = b (J column-major N x N, overwritten by its LU factors; b overwritten by
 // x) by Gaussian elimination with partial pivoting (the largest |pivot| in the
 // column, the first on ties), one CTA.  *singular = 1 when a pivot is zero.
+// SMEM: the matrix and b are copied into shared memory first (N <= kLuSmemMaxN) and
+// x written back at the end; the arithmetic and its order are the same.
 constexpr int kLuThreads = 512;
-__global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restrict__ J, double* __restrict__ b,
+constexpr int kLuSmemMaxN = 160;  // N^2 + N doubles <= 206 KB of shared memory
+template <bool SMEM>
+__global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restrict__ Jg, double* __restrict__ bg,
                                                         int* singular)
 {
     __shared__ double s_val[kLuThreads / 32];
     __shared__ int s_idx[kLuThreads / 32];
     __shared__ int s_piv;
     __shared__ double s_x;
+    extern __shared__ double s_mat[];
+    double* J = Jg;
+    double* b = bg;
+    if constexpr (SMEM) {
+        J = s_mat;
+        b = s_mat + (size_t)N * N;
+        for (int t = threadIdx.x; t < N * N; t += kLuThreads) J[t] = Jg[t];
+        for (int t = threadIdx.x; t < N; t += kLuThreads) b[t] = bg[t];
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int W = kLuThreads / 32;
     auto at = [&](int r, int c) -> double& { return J[(size_t)c * N + r]; };
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restri
         }
         __syncthreads();
         const int pr = s_piv;
-        if (pr >= N) return;  // no pivot at all (all entries NaN): the flag is raised
+        if (pr >= N) return;  // no pivot at all (all entries NaN): the flag is raised, b is left as is
         // swap rows k and pr over columns k..N-1 and b
         if (pr != k) {
             for (int c = k + threadIdx.x; c <= N; c += kLuThreads) {
@@ -566,6 +580,8 @@ __global__ void __launch_bounds__(kLuThreads) k_lu_solve(int N, double* __restri
         }
         __syncthreads();
     }
+    if constexpr (SMEM)
+        for (int t = threadIdx.x; t < N; t += kLuThreads) bg[t] = b[t];
 }
 
 // ------------------------------------------------------------------ velocity update, mixed precision
@@ -1019,7 +1035,13 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
             if (ls != EP_OK) return set_error("ep_match: no Jacobian kernel for this kernel"), ls;
             EP_TRY_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int), st));
             count_launch(2);
-            k_lu_solve<<<1, kLuThreads, 0, st>>>((int)m, dJ, dr, dsing);
+            if (m <= (size_t)kLuSmemMaxN) {
+                const size_t lsm = sizeof(double) * (m * m + m);
+                EP_TRY_CUDA(cudaFuncSetAttribute(k_lu_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+                k_lu_solve<true><<<1, kLuThreads, lsm, st>>>((int)m, dJ, dr, dsing);
+            } else {
+                k_lu_solve<false><<<1, kLuThreads, 0, st>>>((int)m, dJ, dr, dsing);
+            }
             k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dr, h, (int)m);
             EP_TRY_CUDA(cudaGetLastError());
             int sing = 0;
