@@ -49,6 +49,13 @@ MUTANTS = {
     "tangent_dp_sign": ("                dkp[s][a] = -hq[a];", "                dkp[s][a] = hq[a];"),
     "tangent_at_step_start": ("            orc_hvp(dim, kernel, sigma, n, yq, yp, dyq, dyp, hq, hp);",
                               "            orc_hvp(dim, kernel, sigma, n, q1, p1, dyq, dyp, hq, hp);"),
+    # (the line break in front keeps each site unique: the inexact loop's inline copy
+    # of the gain is indented deeper)
+    "default_gain_skips_self": (
+        "\n        for (long j = 0; j < n; ++j) row += fabs(",
+        "\n        for (long j = 0; j < n; ++j) if (j != i) row += fabs("),
+    "default_gain_min_row": ("\n        if (row > best) best = row;", "\n        if (best == 0.0 || row < best) best = row;"),
+    "default_gain_mean_row": ("\n        if (row > best) best = row;", "\n        best += row / (double)n;"),
     "flow_stale_velocity_stage": ("orc_velocity(dim, kernel, sigma, n, yq, yp, m, yx, k4x);",
                                   "orc_velocity(dim, kernel, sigma, n, q1, p1, m, yx, k4x);"),
 }

@@ -266,6 +266,41 @@ def test_match_update_rule_first_iterate():
     assert hist[0] == pytest.approx(np.abs(pr.Y - pr.X).max(), rel=1e-15)
 
 
+def test_default_gain_closed_forms():
+    """The default gain (the Gershgorin bound h = 1 / max_i sum_j G_ij on the largest
+    eigenvalue of G(X), the momentum rule's stability limit h lambda_max < 2 with margin)
+    on configurations whose row sums are known by hand: a lone particle (G(0) = 1, so
+    h = 1), two particles at distance r (both rows 1 + G(r)), three collinear tent
+    particles whose three row sums differ (so the max, the diagonal and the reciprocal
+    each matter), and a 3-4-5 right triangle in 3-D whose right-angle vertex holds the
+    largest row."""
+    for kernel, sigma in KERNELS:
+        assert o.default_gain(np.array([[0.3, 0.7]]), kernel, sigma) == 1.0
+        assert o.default_gain(np.array([[0.3, 0.7, 0.1]]), kernel, sigma) == 1.0
+    r = 0.13
+    two = np.array([[0.2, 0.4], [0.2 + r * 0.6, 0.4 + r * 0.8]])
+    closed = {o.GAUSS: math.exp(-r * r / (2 * 0.3 * 0.3)), o.TENT: 1.0 - r / 0.45, o.EXPCONE: math.exp(-r / 0.4)}
+    for kernel, sigma in KERNELS:
+        assert o.default_gain(two, kernel, sigma) == pytest.approx(1.0 / (1.0 + closed[kernel]), rel=1e-14)
+    # tent sigma = 0.2 at x = 0, 0.1, 0.25: G = 0.5 (0-1), 0.25 (1-2), 0 (0-2, beyond sigma)
+    # row sums 1.5, 1.75, 1.25 -> h = 1 / 1.75
+    line = np.array([[0.0, 0.3], [0.1, 0.3], [0.25, 0.3]])
+    assert o.default_gain(line, o.TENT, 0.2) == pytest.approx(1.0 / 1.75, rel=1e-14)
+    assert o.default_gain(line[::-1].copy(), o.TENT, 0.2) == pytest.approx(1.0 / 1.75, rel=1e-14)
+    # right triangle, legs 0.06 and 0.08, hypotenuse 0.1 (Gaussian sigma = 0.05)
+    tri = np.array([[0.5, 0.5, 0.5], [0.56, 0.5, 0.5], [0.5, 0.58, 0.5]])
+    g = lambda d: math.exp(-d * d / (2 * 0.05 * 0.05))  # noqa: E731
+    rows = [1 + g(0.06) + g(0.08), 1 + g(0.06) + g(0.1), 1 + g(0.08) + g(0.1)]
+    assert o.default_gain(tri, o.GAUSS, 0.05) == pytest.approx(1.0 / max(rows), rel=1e-14)
+    # the bound: 1/h >= lambda_max(G(X)) for a random cloud (Gram matrix from the closed form)
+    q, _ = _cloud(20, 2, seed=41)
+    d = np.linalg.norm(q[:, None] - q[None], axis=-1)
+    lam = np.linalg.eigvalsh(np.exp(-d * d / (2 * 0.3 * 0.3))).max()
+    h = o.default_gain(q, o.GAUSS, 0.3)
+    assert 1.0 / h >= lam * (1 - 1e-12)
+    assert h * lam < 2.0  # the momentum rule's linear stability at the default gain
+
+
 def test_match_reports_divergence():
     """Too large a gain blows up (Table 2, h > 1: NaN); the oracle reports it as a status."""
     pr = w.circle_to_ellipse(32)
