@@ -209,7 +209,9 @@ ep_status ep_cell_neighbors(const ep_params* params, int64_t n, const double* q,
  *  - q, p, dq, dp must be device memory (host arrays return EP_EINVAL);
  *  - the first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *    before any stream capture.  The address is kept per device and context:
+ *    after cudaDeviceReset the next call looks it up again (so it too should
+ *    come before any capture);
  *  - every call shares the one array; calls whose GPU work overlaps (for
  *    example on two unordered streams) race and give wrong results.
  * Results are those of ep_rhs (same kernels). */

@@ -480,17 +480,24 @@ __global__ void k_residual(const double* __restrict__ Y, const double* __restric
     if ((threadIdx.x & 31) == 0) atomicMax(res_bits, mb);
 }
 
-__global__ void k_axpy_update(double* __restrict__ p, const double* __restrict__ delta, double h, int m)
+// p += h delta, unless *skip is set (skip may be NULL): a singular solve leaves
+// delta unfinished, and p0 must stay the last iterate.
+__global__ void k_axpy_update(double* __restrict__ p, const double* __restrict__ delta, double h, int m,
+                              const int* __restrict__ skip)
 {
+    if (skip && *skip) return;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < m) p[e] += h * delta[e];
 }
 
-// Solve J x = b (J column-major N x N, overwritten by its LU factors; b overwritten by
-// x) by Gaussian elimination with partial pivoting (the largest |pivot| in the
-// column, the first on ties), one CTA.  *singular = 1 when a pivot is zero.
-// SMEM: the matrix and b are copied into shared memory first (N <= kLuSmemMaxN) and
-// x written back at the end; the arithmetic and its order are the same.
+// Solve J x = b (J column-major N x N; b overwritten by x) by Gaussian elimination
+// with partial pivoting (the largest |pivot| in the column, the first on ties), one
+// CTA.  *singular = 1 when a pivot is zero; b is then left partly eliminated and
+// must not be used.
+// SMEM = false factors J in place (J holds its LU factors afterwards).  SMEM = true
+// (N <= kLuSmemMaxN) copies J and b into shared memory, factors the copy and writes
+// only x back: J keeps the unfactored matrix.  Callers use x alone and must not rely
+// on J's contents after the call.  The arithmetic and its order are the same.
 constexpr int kLuThreads = 512;
 constexpr int kLuSmemMaxN = 160;  // N^2 + N doubles <= 206 KB of shared memory
 template <bool SMEM>
@@ -1042,20 +1049,20 @@ ep_status rule_match(const ep_params& P, int64_t n, const double* X, const doubl
             } else {
                 k_lu_solve<false><<<1, kLuThreads, 0, st>>>((int)m, dJ, dr, dsing);
             }
-            k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dr, h, (int)m);
+            k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dr, h, (int)m, dsing);
             EP_TRY_CUDA(cudaGetLastError());
             int sing = 0;
             EP_TRY_CUDA(cudaMemcpyAsync(&sing, dsing, sizeof(int), cudaMemcpyDeviceToHost, st));
             EP_TRY_CUDA(cudaStreamSynchronize(st));
             info->products += (int)m;
-            ++k;
             if (sing) {
+                // no update was applied: p0 is the iterate of the last shoot
                 set_error("ep_match: the shooting Jacobian is singular after %d updates", k);
                 singular = true;
                 status = EP_EDIVERGED;
-                res = NAN;
                 break;
             }
+            ++k;
             continue;
         }
         int used = 0;
@@ -1169,7 +1176,7 @@ ep_status velocity_mixed_match(const ep_params& P, int64_t n, const double* X, c
         if (k == info->maxit) { status = EP_ENOTCONVERGED; break; }
         count_launch(2);
         k_gram_solve<<<1, 32, 0, st>>>((int)n, P.dim, Gm, piv, dr, dl, dk);
-        k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dl, h, (int)m);
+        k_axpy_update<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(dp, dl, h, (int)m, nullptr);
         EP_TRY_CUDA(cudaGetLastError());
         info->products += P.dim;
         ++k;

@@ -35,24 +35,61 @@ constexpr size_t kNoAllocScratchBytes = 1280 * 1024;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_mu;
-std::map<int, void*> g_addr;  // device -> device address of g_noalloc_scratch
+// (device, context id) -> device address of g_noalloc_scratch.  The context id
+// is part of the key because cudaDeviceReset (or any destruction and re-creation
+// of the primary context) loads the module again, possibly at another address.
+std::map<std::pair<int, unsigned long long>, void*> g_addr;
 
-// Set-up, once per device, with that device current: look up the array's
-// device address.  In host code the symbol is only a host-side stand-in.
+// The current context's id (cuCtxGetId, unique for the life of the process), by
+// way of the runtime's driver entry points so that the library needs no link
+// against the driver library.  0 when the driver does not provide it.
+unsigned long long current_context_id()
+{
+    typedef int (*ctx_get_current_t)(void**);
+    typedef int (*ctx_get_id_t)(void*, unsigned long long*);
+    static ctx_get_current_t get_current = nullptr;
+    static ctx_get_id_t get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (ctx_get_current_t)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (ctx_get_id_t)f;
+        cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Set-up, once per device (and per context on it), with that device current:
+// look up the array's device address.  In host code the symbol is only a
+// host-side stand-in.  Before the first runtime call on a thread no context may
+// be current (id 0): the lookup then creates the primary context, and the entry
+// is stored under the id of the context it was made in.
 ep_status scratch_address(void** out)
 {
     int dev = 0;
     EP_TRY_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_addr.find(dev);
-    if (it != g_addr.end()) {
-        *out = it->second;
-        return EP_OK;
+    const unsigned long long id = current_context_id();
+    if (id != 0) {
+        auto it = g_addr.find(std::make_pair(dev, id));
+        if (it != g_addr.end()) {
+            *out = it->second;
+            return EP_OK;
+        }
     }
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_addr[dev] = p;
+    g_addr[std::make_pair(dev, current_context_id())] = p;
     *out = p;
     return EP_OK;
 }

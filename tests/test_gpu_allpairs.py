@@ -111,6 +111,27 @@ def test_shoot_full_size_fourier_curve_mixed():
     assert np.abs(q1.cpu().numpy() - rq).max() < 1e-6
 
 
+def test_benchmark_match_per_iterate_parity():
+    """The benchmarked call itself: ep_match of the N = 4096 Fourier-curve workload
+    (Gaussian sigma = 0.1, 100 RK4 steps, mixed precision, all pairs, the default
+    gain, p0 = 0), i.e. the persistent all-pairs shoot with the FP64 residual and
+    momentum update of Algorithm 1, stopped after 2 updates.  The residual of each
+    of the 3 shoots and the momenta after the last update agree with the oracle's
+    Algorithm 1 element by element within the shot-endpoint bound 1e-4."""
+    pr = w.fourier_curve_warp()
+    maxit = 2
+    prm = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=pr.steps, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    r = ep.match(cuda(pr.X), cuda(pr.Y), prm, h=0.0, eps=pr.eps, maxit=maxit)
+    h_ref = o.default_gain(pr.X, pr.kernel, pr.sigma)
+    assert abs(r.h - h_ref) < 1e-6 * h_ref
+    p, st, it, res, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=h_ref, eps=pr.eps, maxit=maxit)
+    assert r.status == st == ep.ENOTCONVERGED and r.iters == it == maxit
+    assert len(r.hist) == len(hist) == maxit + 1
+    np.testing.assert_allclose(r.hist, hist, rtol=1e-4)
+    assert rel(r.p0, p) < 1e-4
+    assert np.abs(r.p0.cpu().numpy() - p).max() < 1e-4 * np.abs(p).max()
+
+
 def test_shoot_aliasing_and_host_pointers():
     q, p = cloud(100, 2, seed=3)
     prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=5, precision=ep.FP64)

@@ -325,6 +325,41 @@ def test_newton_rule_at_the_dense_threshold(extra):
     np.testing.assert_allclose(res.hist, hist, rtol=1e-8)
 
 
+@pytest.mark.parametrize("extra", [0, 1])
+def test_newton_rule_at_the_shared_memory_lu_threshold(extra):
+    # 80 landmarks (n dim = 160): the LU runs on a shared-memory copy of D phi (the
+    # largest, ~206 KB); 81 (162): in global memory.  Two Newton updates on each side.
+    X = _grid(10, 8, 0.04, extra)
+    Y = X + 0.002 * np.random.default_rng(13).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.03, steps=4, precision=ep.FP64, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_NEWTON, h=1.0, eps=0.0, maxit=2)
+    rp, st, it, r, hist = o.match_newton(X, Y, ep.GAUSS, 0.03, 4, h=1.0, eps=0.0, maxit=2)
+    assert X.size == (162 if extra else 160)
+    assert res.iters == it == 2
+    assert res.products == 2 * X.size
+    assert rel(res.p0, rp) < 1e-8
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-8)
+
+
+@pytest.mark.parametrize("n,prec", [(2, ep.FP64), (82, ep.FP64), (2, ep.MIXED)])
+def test_newton_singular_jacobian_keeps_the_last_iterate(n, prec):
+    # Two coincident landmarks: at p0 = 0 the shoot is Q(1) = X + G(X) p0 to first order,
+    # so D phi has two equal rows and columns and the elimination meets an exact zero
+    # pivot.  The match returns EP_EDIVERGED with p0 left at the iterate it was shot
+    # from (the initial guess), no update counted, and that shoot's finite residual.
+    # n dim = 4 factors in shared memory, 164 in global memory.
+    X = _grid(9, 9, 0.05, 0)[: n - 1] if n > 2 else np.array([[0.4, 0.5]])
+    X = np.vstack([X, X[-1:]])
+    Y = X + 0.01 * np.random.default_rng(14).normal(size=X.shape)
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=0.12, steps=5, precision=prec, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_NEWTON, h=1.0, eps=1e-9, maxit=5)
+    assert res.status == ep.EDIVERGED
+    assert res.iters == 0
+    assert np.all(host(res.p0) == 0.0)
+    assert np.isfinite(res.resid) and res.resid == pytest.approx(np.abs(Y - X).max(), rel=1e-6)
+    assert "singular" in ep.last_error()
+
+
 # --------------------------------------------------------------------------- mixed precision (Newton)
 
 
