@@ -47,8 +47,16 @@ typedef enum {
 typedef enum { EP_GAUSS = 0, EP_TENT = 1, EP_EXPCONE = 2 } ep_kernel;
 
 /* EP_FP64: every operation in FP64 (the plain comparison path).
- * EP_MIXED: pair terms in FP32, per-particle sums accumulated in FP64, RK4
- *           step state in FP64, feedback residual and momentum update in FP64. */
+ * EP_MIXED: pair terms in FP32; each per-particle sum of the all-pairs right-hand
+ *           side (and of the adjoint's Hessian products) is formed in FP32 over
+ *           blocks of at most 256 sources per warp, and the blocks are accumulated
+ *           in compensated double-FP32 (TwoSum) arithmetic and, across thread
+ *           blocks, in FP64, so the sums carry FP64-level accumulation error
+ *           whatever n is; the batched solver folds FP32 runs of 512 sources into
+ *           FP64; the cell list sums each particle's at most nine neighbour cells
+ *           in FP32 (a bounded block).  The RK4 stage combination is FP32 on the
+ *           sums rounded once; the step state, the feedback residual and the
+ *           momentum update are FP64. */
 typedef enum { EP_FP64 = 0, EP_MIXED = 1 } ep_precision;
 
 /* EP_AUTO picks the cell list for EP_TENT when it pays off, else all-pairs. */
@@ -114,6 +122,11 @@ typedef struct {
                         Newton; MINRES Gram products, or one solve per component and
                         update with the factored G(X), for the velocity rule; 0 for the
                         momentum rule */
+    int status;      /* out: ep_status of this matching (Algorithm 1 steps 2-3: EP_OK when
+                        max|Y - Q(1)| < eps was reached, EP_ENOTCONVERGED at the iteration
+                        cap, EP_EDIVERGED on a non-finite residual or a singular solve).
+                        ep_match sets it to its return value; ep_match_batched sets it per
+                        problem (its return value is the first non-OK one) */
 } ep_match_info;
 
 /* Right-hand side of the N-particle system (Sec. 3.1, Eq. N-particle):
@@ -169,7 +182,8 @@ ep_status ep_adjoint(const ep_params* params, int64_t n, const double* X, const 
  * arrays; infos[b].hist is ignored).  Limits: dim = 2, EP_MIXED, n_b <= 8192.  offsets: host array of nprob+1
  * int64 with offsets[0] = 0, non-decreasing.  All problems must share dim.
  * Synchronises the stream.  Returns EP_OK when every problem converged, else
- * the first non-OK status in problem order. */
+ * the first non-OK status in problem order; infos[b].status holds problem b's own
+ * status (set by the solver on the device). */
 ep_status ep_match_batched(const ep_params* params, int nprob, const int64_t* offsets,
                            const double* X, const double* Y, double* p0, ep_match_info* infos,
                            void* stream);

@@ -38,6 +38,10 @@ namespace {
 
 constexpr int kHvpThreads = 512;
 constexpr int kHvpChunk = 1024;
+// A warp's FP32 block of a particle's HVP sums covers kHvpFoldChunks staged chunks
+// (kHvpFoldChunks * kHvpChunk / 16 = 256 sources); the blocks are accumulated in
+// double-FP32 across warps and blocks and in FP64 across CTAs.
+constexpr int kHvpFoldChunks = 4;
 constexpr float kLog2e = 1.4426950408889634f;
 
 enum HvpMode { HVP_STAGE = 0, HVP_SINGLE = 1 };
@@ -218,6 +222,7 @@ __global__ void __launch_bounds__(kHvpThreads, 1) k_hvp_mixed(HvpArgs a)
     constexpr int V = DIM == 2 ? 1 : 2;  // float4 per particle per record
     extern __shared__ float4 smem[];     // [chunk][state V | direction V]
     __shared__ int s_last;
+    __shared__ float2 fin[2 * DIM * kTileI];  // double-FP32 sums of the tile's segment
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.n;
     long long u0 = (long long)blockIdx.x * a.U / a.G;
@@ -242,6 +247,8 @@ __global__ void __launch_bounds__(kHvpThreads, 1) k_hvp_mixed(HvpArgs a)
         for (int r = 0; r < 2; ++r)
 #pragma unroll
             for (int c = 0; c < DIM; ++c) hq[r][c] = hp[r][c] = 0.f;
+        int nchunk = 0;
+        bool first = true;
         for (int cj = j0; cj < j1; cj += kHvpChunk) {
             const int L = min(kHvpChunk, j1 - cj);
             __syncthreads();
@@ -279,24 +286,33 @@ __global__ void __launch_bounds__(kHvpThreads, 1) k_hvp_mixed(HvpArgs a)
                     }
                 }
             }
-        }
-        __syncthreads();
-        float* red = reinterpret_cast<float*>(smem);  // [W][2*DIM][64]
+            // fold the lanes' FP32 blocks: every kHvpFoldChunks chunks and at the segment end
+            if (++nchunk % kHvpFoldChunks != 0 && cj + kHvpChunk < j1) continue;
+            __syncthreads();
+            float* red = reinterpret_cast<float*>(smem);  // [W][2*DIM][64]
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) {
-                red[(warp * 2 * DIM + c) * kTileI + lane + 32 * r] = hq[r][c];
-                red[(warp * 2 * DIM + DIM + c) * kTileI + lane + 32 * r] = hp[r][c];
+                for (int c = 0; c < DIM; ++c) {
+                    red[(warp * 2 * DIM + c) * kTileI + lane + 32 * r] = hq[r][c];
+                    red[(warp * 2 * DIM + DIM + c) * kTileI + lane + 32 * r] = hp[r][c];
+                    hq[r][c] = hp[r][c] = 0.f;
+                }
+            __syncthreads();
+            for (int t = threadIdx.x; t < 2 * DIM * kTileI; t += kHvpThreads) {
+                float2 sum = make_float2(red[t], 0.f);
+                for (int w2 = 1; w2 < W; ++w2) dd_acc(sum, red[w2 * 2 * DIM * kTileI + t]);
+                fin[t] = first ? dd_add(sum, make_float2(0.f, 0.f)) : dd_add(fin[t], sum);
             }
-        __syncthreads();
+            first = false;
+        }
+        // the segment's sums into the FP64 accumulator (each fin entry is read by the
+        // thread that wrote it)
         for (int t = threadIdx.x; t < 2 * DIM * kTileI; t += kHvpThreads) {
             const int k = t / kTileI, il = t % kTileI;
-            float sum = 0.f;
-            for (int w2 = 0; w2 < W; ++w2) sum += red[(w2 * 2 * DIM + k) * kTileI + il];
             const int i = b * kTileI + il;
             const int slot = k < DIM ? k : 3 + (k - DIM);
-            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + slot, (double)sum);
+            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + slot, dd_to_double(fin[t]));
         }
         __threadfence();
         __syncthreads();

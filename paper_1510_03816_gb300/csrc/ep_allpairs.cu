@@ -7,11 +7,13 @@
 // U = ntiles * n units (tile b, source j), cut into G equal contiguous ranges,
 // one per CTA, G = (SM count) x (resident CTAs per SM).  A CTA's range covers
 // one or a few tile segments [j0, j1).  For each segment the CTA stages the
-// FP32 source data of [j0, j1) in shared memory, its warps split the j range,
-// every lane accumulates its two particles' sums in registers (FP32), the
-// warps' partials are summed in shared memory, and the CTA adds its partial
-// into the FP64 accumulator K of the tile's particles (red.global.add.f64:
-// the per-particle sums are accumulated in FP64).  The last CTA to arrive at
+// FP32 source data of [j0, j1) in shared memory, chunk by chunk; its warps split
+// a chunk's j range, every lane accumulates its two particles' sums over its
+// share in registers (FP32), the warps' partials are summed in double-FP32
+// (TwoSum) in shared memory, and the CTA adds them, converted exactly to FP64,
+// into the FP64 accumulator K of the tile's particles (red.global.add.f64): the
+// per-particle sums are accumulated in FP64 across blocks of at most
+// kChunk / warps sources.  The last CTA to arrive at
 // a tile (per-tile counter) applies the RK4 stage to the tile's particles:
 // it reads k = K, forms the next stage input, resets K and the counter.
 //
@@ -77,17 +79,17 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                 for (int c = 0; c < DIM; ++c) { qi[r][c] = 0.0f; pi[r][c] = 0.0f; }
             }
         }
-        float acc[2][kKWidth];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int t = 0; t < kKWidth; ++t) acc[r][t] = 0.0f;
-
         for (int cj = j0; cj < j1; cj += kChunk) {
             const int L = min(kChunk, j1 - cj);
             __syncthreads();
             for (int t = threadIdx.x; t < L * V; t += THREADS) smem[t] = __ldcg(a.S_in + (size_t)cj * V + t);
             __syncthreads();
+            // the lane's two particles' sums over this chunk's warp share, FP32
+            float acc[2][kKWidth];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int t = 0; t < kKWidth; ++t) acc[r][t] = 0.0f;
             const int ja = warp * L / W, jb = (warp + 1) * L / W;
 #pragma unroll 4
             for (int j = ja; j < jb; ++j) {
@@ -126,23 +128,23 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                     }
                 }
             }
-        }
-
-        // warps' partials -> shared memory [W][6][64] -> FP64 accumulator
-        __syncthreads();
-        float* red = reinterpret_cast<float*>(smem);
+            // warps' partials -> shared memory [W][6][64] -> double-FP32 over the warps ->
+            // the FP64 accumulator (exact conversion)
+            __syncthreads();
+            float* red = reinterpret_cast<float*>(smem);
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int t = 0; t < kKWidth; ++t) red[(warp * kKWidth + t) * kTileI + lane + 32 * r] = acc[r][t];
-        __syncthreads();
-        for (int t = threadIdx.x; t < kKWidth * kTileI; t += THREADS) {
-            const int k = t / kTileI, il = t % kTileI;
-            float s = 0.0f;
+                for (int t = 0; t < kKWidth; ++t) red[(warp * kKWidth + t) * kTileI + lane + 32 * r] = acc[r][t];
+            __syncthreads();
+            for (int t = threadIdx.x; t < kKWidth * kTileI; t += THREADS) {
+                const int k = t / kTileI, il = t % kTileI;
+                float2 sum = make_float2(0.0f, 0.0f);
 #pragma unroll 8
-            for (int w2 = 0; w2 < W; ++w2) s += red[(w2 * kKWidth + k) * kTileI + il];
-            const int i = b * kTileI + il;
-            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, (double)s);
+                for (int w2 = 0; w2 < W; ++w2) dd_acc(sum, red[(w2 * kKWidth + k) * kTileI + il]);
+                const int i = b * kTileI + il;
+                if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, dd_to_double(dd_add(sum, make_float2(0.f, 0.f))));
+            }
         }
         if constexpr (LAST) {
             __threadfence();
@@ -175,7 +177,10 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 // are (32 / JL) row groups x JL source lanes; a lane holds 4 rows (row group g:
 // rows g, g + 32/JL, ...) and takes every JL-th source of its warp's share, so each
 // staged source record feeds 4 particles of the lane.  The source lanes and the
-// warps are reduced after the sub-tile (shuffles, then shared memory).
+// warps are reduced after the sub-tile: a warp's block of a particle's sum (its
+// n / W sources, at most 256 since n <= kOwnerMaxN) is FP32 (lane sums, then
+// shuffles over the source lanes); the W blocks are accumulated in double-FP32
+// (TwoSum) in shared memory, to FP64-level accuracy.
 //
 // Factored Gaussian on coordinates centred on the sub-tile's first particle,
 // q'' = q' - q'_first: with G = 2^-|q''_i - q''_j|^2 (scaled units),
@@ -213,23 +218,32 @@ __device__ __forceinline__ EpiIn epi_load(const StageArgs& a, int i, int comp)
     return e;
 }
 
-// RK4 stage of component comp (0, 1: q; 2, 3: p) of particle i from its six FP32
-// pair sums f (dq_x, dq_y, M_xx, M_xy, M_yx, M_yy): the 2-D mixed epilogue with
-// one thread per component.  Only the step update (stage 3) touches FP64.
-__device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int comp, const float* f, const EpiIn& e)
+// RK4 stage of component comp (0, 1: q; 2, 3: p) of particle i from its six pair
+// sums f (dq_x, dq_y, M_xx, M_xy, M_yx, M_yy), each a double-FP32 value: the 2-D
+// mixed epilogue with one thread per component.  One RHS (MODE_RHS) evaluates the
+// result in FP64 from the pairs; the RK4 stage combination takes each sum rounded
+// once to FP32 (its hi part) and only the step update (stage 3) touches FP64.
+__device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int comp, const float2* f, const EpiIn& e)
 {
+    if (a.mode == MODE_RHS) {
+        double kv;
+        if (comp < 2) {
+            kv = dd_to_double(comp == 0 ? f[0] : f[1]) + a.s2 * (double)(comp == 0 ? e.pin.x : e.pin.y);  // + sigma_n^2 p_i (Sec. 6)
+        } else {
+            const double m0 = dd_to_double(comp == 2 ? f[2] : f[4]), m1 = dd_to_double(comp == 2 ? f[3] : f[5]);
+            kv = a.dp_scale * (m0 * (double)e.pin.x + m1 * (double)e.pin.y);
+        }
+        double* out = comp < 2 ? a.out_q : a.out_p;
+        out[(size_t)i * 2 + (comp & 1)] = kv;
+        return;
+    }
     float kv;
     if (comp < 2) {
         // dq (+ sigma_n^2 p_i for the inexact system, Sec. 6)
-        kv = fmaf(a.s2_f, comp == 0 ? e.pin.x : e.pin.y, comp == 0 ? f[0] : f[1]);
+        kv = fmaf(a.s2_f, comp == 0 ? e.pin.x : e.pin.y, comp == 0 ? f[0].x : f[1].x);
     } else {
-        const float m0 = comp == 2 ? f[2] : f[4], m1 = comp == 2 ? f[3] : f[5];
+        const float m0 = comp == 2 ? f[2].x : f[4].x, m1 = comp == 2 ? f[3].x : f[5].x;
         kv = a.dp_scale_f * fmaf(m0, e.pin.x, m1 * e.pin.y);
-    }
-    if (a.mode == MODE_RHS) {
-        double* out = comp < 2 ? a.out_q : a.out_p;
-        out[(size_t)i * 2 + (comp & 1)] = (double)kv;
-        return;
     }
     float* A = a.acc + (size_t)i * 4 + comp;
     if (a.stage < 3) {
@@ -259,7 +273,7 @@ template <int THREADS, int JL>
 constexpr size_t owner_smem()
 {
     return (size_t)owner_chunk<JL>() * (2 * sizeof(float4) + sizeof(float)) +
-           (size_t)(THREADS / 32 + 1) * kKWidth * ((32 / JL) * 4) * sizeof(float);
+           (size_t)(THREADS / 32 + 2) * kKWidth * ((32 / JL) * 4) * sizeof(float);
 }
 
 template <int THREADS, int JL>
@@ -273,8 +287,8 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
     constexpr int NV = RI * kKWidth;  // finalized partials per lane
     float4* recA = smem;                                    // [2 * CH]
     float* recB = reinterpret_cast<float*>(smem + 2 * CH);  // [CH]
-    float* red = recB + CH;                                 // [W][6][R], then fin [6][R]
-    float* fin = red + (size_t)W * kKWidth * R;
+    float* red = recB + CH;                                 // [W][6][R]: the warps' FP32 blocks
+    float2* fin = reinterpret_cast<float2*>(red + (size_t)W * kKWidth * R);  // [6][R]: double-FP32 sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rg = lane / JL, jl = lane % JL;
     const int n = a.n;
@@ -404,17 +418,22 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
             }
         }
         __syncthreads();
-        // sum over the warps: QS threads per output value
+        // sum over the warps in double-FP32 (QS threads per output value): the per-particle
+        // sums are accumulated across the warps' FP32 blocks with TwoSum error terms
         constexpr int NOUT = kKWidth * R;
         constexpr int QS = (THREADS / NOUT) >= 8 ? 8 : (THREADS / NOUT) >= 4 ? 4 : (THREADS / NOUT) >= 2 ? 2 : 1;
         for (int t = threadIdx.x; t < NOUT * QS; t += THREADS) {
             const int o = t / QS, q = t % QS;
-            float sum = 0.0f;
+            float2 sum = make_float2(red[q * NOUT + o], 0.0f);
 #pragma unroll
-            for (int w2 = q; w2 < W; w2 += QS) sum += red[w2 * NOUT + o];
+            for (int w2 = q + QS; w2 < W; w2 += QS) dd_acc(sum, red[w2 * NOUT + o]);
 #pragma unroll
-            for (int m = QS / 2; m >= 1; m >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, m);
-            if (q == 0) fin[o] = sum;
+            for (int m = QS / 2; m >= 1; m >>= 1) {
+                const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, sum.x, m),
+                                                 __shfl_xor_sync(0xffffffffu, sum.y, m));
+                sum = dd_add(sum, other);
+            }
+            if (q == 0) fin[o] = QS == 1 ? dd_add(sum, make_float2(0.0f, 0.0f)) : sum;
         }
         __syncthreads();
         // the RK4 stage of the sub-tile's rows, one thread per component
@@ -422,7 +441,7 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
             const int rl = threadIdx.x >> 2, comp = threadIdx.x & 3;
             const int i = t0 + rl;
             if (i < t1) {
-                float f[kKWidth];
+                float2 f[kKWidth];
 #pragma unroll
                 for (int k = 0; k < kKWidth; ++k) f[k] = fin[k * R + rl];
                 epilogue2_comp(a, i, comp, f, epi_load(a, i, comp));
@@ -493,11 +512,6 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
             mq = fmaxf(mq, fmaf(qx[r], qx[r], qy[r] * qy[r]));
         }
         const bool factored = !__syncthreads_or(mq > kFactorMax);
-        // per particle: (sum g px, sum g py), (sum g x px, sum g x py), (sum g y px, sum g y py),
-        // packed so every accumulation is one f32x2 FMA
-        float2 sqv[RI], sbx[RI], sby[RI];
-#pragma unroll
-        for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
         for (int cj = j0; cj < j1; cj += kChunkG) {
             const int L = min(kChunkG, j1 - cj);
             __syncthreads();
@@ -509,6 +523,11 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
                 recB[t] = y * v.w;
             }
             __syncthreads();
+            // per particle: (sum g px, sum g py), (sum g x px, sum g x py), (sum g y px, sum g y py),
+            // packed so every accumulation is one f32x2 FMA; FP32 over this chunk's warp share
+            float2 sqv[RI], sbx[RI], sby[RI];
+#pragma unroll
+            for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
             const int ja = warp * L / W, jb = (warp + 1) * L / W;
             if (factored) {
 #pragma unroll 2
@@ -545,30 +564,31 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
                     }
                 }
             }
-        }
-        // per particle: dq = E sq, M = q'' (x) dq - E sb  (E = 1 in the difference form)
-        __syncthreads();
-        float* red = reinterpret_cast<float*>(smem);  // [W][6][kTileG]
+            // per particle: dq = E sq, M = q'' (x) dq - E sb  (E = 1 in the difference form)
+            __syncthreads();
+            float* red = reinterpret_cast<float*>(smem);  // [W][6][kTileG]
 #pragma unroll
-        for (int r = 0; r < RI; ++r) {
-            const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
-            const float d0 = E * sqv[r].x, d1 = E * sqv[r].y;
-            float* o = red + (size_t)warp * kKWidth * kTileG + lane + 32 * r;
-            o[0 * kTileG] = d0;
-            o[1 * kTileG] = d1;
-            o[2 * kTileG] = fmaf(qx[r], d0, -E * sbx[r].x);
-            o[3 * kTileG] = fmaf(qx[r], d1, -E * sbx[r].y);
-            o[4 * kTileG] = fmaf(qy[r], d0, -E * sby[r].x);
-            o[5 * kTileG] = fmaf(qy[r], d1, -E * sby[r].y);
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < kKWidth * kTileG; t += THREADS) {
-            const int k = t / kTileG, il = t % kTileG;
-            float sum = 0.0f;
+            for (int r = 0; r < RI; ++r) {
+                const float E = factored ? ex2_approx(-fmaf(qx[r], qx[r], qy[r] * qy[r])) : 1.0f;
+                const float d0 = E * sqv[r].x, d1 = E * sqv[r].y;
+                float* o = red + (size_t)warp * kKWidth * kTileG + lane + 32 * r;
+                o[0 * kTileG] = d0;
+                o[1 * kTileG] = d1;
+                o[2 * kTileG] = fmaf(qx[r], d0, -E * sbx[r].x);
+                o[3 * kTileG] = fmaf(qx[r], d1, -E * sbx[r].y);
+                o[4 * kTileG] = fmaf(qy[r], d0, -E * sby[r].x);
+                o[5 * kTileG] = fmaf(qy[r], d1, -E * sby[r].y);
+            }
+            __syncthreads();
+            // the warps' blocks in double-FP32, added to K in FP64 (exact conversion)
+            for (int t = threadIdx.x; t < kKWidth * kTileG; t += THREADS) {
+                const int k = t / kTileG, il = t % kTileG;
+                float2 sum = make_float2(0.0f, 0.0f);
 #pragma unroll 8
-            for (int w2 = 0; w2 < W; ++w2) sum += red[(w2 * kKWidth + k) * kTileG + il];
-            const int i = b * kTileG + il;
-            if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, (double)sum);
+                for (int w2 = 0; w2 < W; ++w2) dd_acc(sum, red[(w2 * kKWidth + k) * kTileG + il]);
+                const int i = b * kTileG + il;
+                if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, dd_to_double(dd_add(sum, make_float2(0.f, 0.f))));
+            }
         }
         u0 += (j1 - j0);
     }
@@ -1234,11 +1254,16 @@ ep_status launch_owner_cfg(const StageArgs& a, const AllPairsBufs& b, int steps,
     return launch_owner<4>(a2, b, steps, st, done, ev0, ev1, rec);
 }
 
+// Largest n of the owner-computes kernel: a warp's FP32 block of a particle's sum
+// covers n / 32 sources (the lane sums run over every staged chunk), at most 256.
+constexpr int kOwnerMaxN = 8192;
+
 // Default owner configuration: the widest sub-tile the rows per SM fill, and the
-// CTA count that fills each CTA's sub-tiles.
+// CTA count that fills each CTA's sub-tiles; stream-K (JL = 0) beyond kOwnerMaxN.
 OwnerCfg owner_default(int n, int sm)
 {
     OwnerCfg c;
+    if (n > kOwnerMaxN) return OwnerCfg{sm, 0};
     const double per = (double)n / sm;
     c.JL = per >= 96 ? 1 : per >= 24 ? 4 : 16;
     const int R = (32 / c.JL) * 4;
@@ -1305,6 +1330,7 @@ ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a
         for (int g : gs) cand.push_back(OwnerCfg{g, 0});
     } else {
         for (int JL : {1, 4, 16}) {
+            if (n > kOwnerMaxN) break;
             const int R = (32 / JL) * 4;
             const long long k = std::max<long long>(1, (n + (long long)sm * R - 1) / ((long long)sm * R));
             const int g1 = (int)std::max<long long>(1, std::min<long long>(sm, (n + k * R - 1) / (k * R)));

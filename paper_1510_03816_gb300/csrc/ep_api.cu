@@ -489,8 +489,8 @@ ep_status ep_hamiltonian(const ep_params* params, int64_t n, const double* q, co
     return EP_OK;
 }
 
-ep_status ep_match(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
-                   ep_match_info* info, void* stream)
+static ep_status match_entry(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
+                             ep_match_info* info, void* stream)
 {
     EP_TRY(check_params(params));
     EP_TRY(check_n(n));
@@ -640,6 +640,14 @@ ep_status ep_adjoint(const ep_params* params, int64_t n, const double* X, const 
                      double lambda, int ckpt_every, double* grad_p0, double* energy, void* stream)
 {
     return adjoint_entry(params, n, X, p0, Y, lambda, ckpt_every, grad_p0, energy, stream);
+}
+
+ep_status ep_match(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
+                   ep_match_info* info, void* stream)
+{
+    const ep_status s = match_entry(params, n, X, Y, p0, info, stream);
+    if (info) info->status = (int)s;
+    return s;
 }
 
 ep_status ep_match_batched(const ep_params* params, int nprob, const int64_t* offsets, const double* X,

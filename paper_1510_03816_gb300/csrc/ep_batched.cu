@@ -702,6 +702,7 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     EP_TRY_CUDA(cudaGetLastError());
     ep_status first = EP_OK;
     for (int b = 0; b < nprob; ++b) {
+        infos[b].status = outs[b].status;
         infos[b].iters = outs[b].iters;
         infos[b].resid_inf = outs[b].resid;
         infos[b].H = outs[b].H;

@@ -100,6 +100,47 @@ struct Sizer {
     void add(size_t bytes) { total += (bytes + 255) & ~size_t(255); }
 };
 
+// ---- compensated (double-FP32) accumulation of the per-particle sums
+// A value is an unevaluated pair (hi, lo) of floats whose exact sum carries ~48
+// significant bits; the intrinsics keep the compiler from contracting or
+// reassociating the error terms.  The lane sums over one staged chunk are FP32;
+// every sum across warps, chunks and CTAs goes through these, so a particle's
+// sum is accumulated to FP64-level accuracy whatever n is.
+//
+// Error-free transformation of a sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float& e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// acc += b (cascaded: the rounding errors gather in acc.y; no renormalisation)
+__device__ __forceinline__ void dd_acc(float2& acc, float b)
+{
+    float e;
+    acc.x = two_sum(acc.x, b, e);
+    acc.y = __fadd_rn(acc.y, e);
+}
+
+// a + b, renormalised so that hi is the float nearest to the pair's value
+__device__ __forceinline__ float2 dd_add(float2 a, float2 b)
+{
+    float e;
+    const float s = two_sum(a.x, b.x, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+// The pair's value in FP64 (exact for a renormalised pair, whose two parts span at
+// most 48 bits).
+__device__ __forceinline__ double dd_to_double(float2 a)
+{
+    return (double)a.x + (double)a.y;
+}
+
 // ---------------------------------------------------------------- validation
 ep_status check_params(const ep_params* p);
 

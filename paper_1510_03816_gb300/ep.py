@@ -53,7 +53,7 @@ class MatchInfo(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("eps", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("iters", ctypes.c_int), ("resid_inf", ctypes.c_double), ("H", ctypes.c_double),
                 ("hist", ctypes.c_void_p), ("rule", ctypes.c_int), ("krylov", ctypes.c_int),
-                ("products", ctypes.c_int)]
+                ("products", ctypes.c_int), ("status", ctypes.c_int)]
 
 
 # ep_rule: the update of Algorithm 1 step 3 (p0 += h r, h G(X)^-1 r, h (D phi)^-1 r)
@@ -388,8 +388,7 @@ def match_batched(Xs, Ys, prms, h=0.0, eps: float = 1e-6, maxit: int = 200):
     for b in range(nprob):
         sl = slice(int(offs[b]), int(offs[b + 1]))
         inf = infos[b]
-        bst = OK if inf.resid_inf < eps else (EDIVERGED if not np.isfinite(inf.resid_inf) else ENOTCONVERGED)
-        out.append(MatchResult(p[sl], bst, inf.iters, inf.resid_inf, inf.H, inf.h, None))
+        out.append(MatchResult(p[sl], int(inf.status), inf.iters, inf.resid_inf, inf.H, inf.h, None))
     return out
 
 

@@ -92,9 +92,10 @@ def test_shoot_parity(prec, kernel, sigma, dim):
     prm = ep.params(dim=dim, kernel=kernel, sigma=sigma, steps=8, precision=prec, neigh=ep.ALLPAIRS)
     q1, p1 = ep.shoot(cuda(q), cuda(p), prm)
     rq, rp = o.shoot(q, p, kernel, sigma, 8)
+    # the tent's momentum weight jumps at r = sigma; the mixed shoot still meets the
+    # endpoint bound (measured <= 6e-7: a stage evaluation would have to land within
+    # FP32 rounding of the kink for FP32 and FP64 to take different sides)
     tol = TOL[prec]["shoot"]
-    if kernel == ep.TENT and prec == ep.MIXED:
-        tol = 1e-3  # the tent's momentum weight is discontinuous at r = sigma
     assert rel(q1, rq) < tol
     assert rel(p1, rp) < tol
 
@@ -160,7 +161,7 @@ def test_match_per_iterate_parity_circle_to_ellipse(prec):
     assert r.status == st and r.iters == it
     tol = 1e-12 if prec == ep.FP64 else 1e-4
     assert rel(r.p0, p) < tol
-    np.testing.assert_allclose(r.hist, hist, rtol=tol if prec == ep.FP64 else 1e-3)
+    np.testing.assert_allclose(r.hist, hist, rtol=tol)
     assert abs(r.H - o.hamiltonian(pr.X, p, pr.kernel, pr.sigma)) < 10 * tol * abs(r.H)
 
 

@@ -1,7 +1,7 @@
 """ep_match_batched: many independent matchings of uneven size in one persistent
 launch, checked per problem against the FP64 oracle (and the single-problem
-GPU path) through the C ABI.  Mixed precision: momenta <= 1e-4 relative
-(1e-3 for the tent, whose momentum weight jumps at r = sigma)."""
+GPU path) through the C ABI.  Mixed precision: momenta <= 1e-4 relative for
+both kernels."""
 import numpy as np
 import pytest
 
@@ -50,7 +50,7 @@ def run_batched(prs, h, eps, maxit, cuda=True):
 
 def test_batched_per_problem_parity_with_oracle():
     """Solo problems (n < 2048, one CTA each) and team problems (n >= 2048, a whole
-    8-CTA cluster with distributed shared memory) against the oracle."""
+    cluster of CTAs with distributed shared memory) against the oracle."""
     sizes = [32, 33, 97, 256, 500, 1023, 1500, 2047, 2048, 2600]
     prs = problems(sizes, steps=4)
     res = run_batched(prs, 0.0, eps=1e-12, maxit=3)  # default gain per problem
@@ -58,7 +58,7 @@ def test_batched_per_problem_parity_with_oracle():
         assert abs(r.h - o.default_gain(pr.X, pr.kernel, pr.sigma)) < 1e-6 * r.h
         p, st, it, resid, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=r.h, eps=1e-12, maxit=3)
         assert r.iters == it == 3
-        tol = 1e-3 if pr.kernel == ep.TENT else 1e-4
+        tol = 1e-4  # both kernels (tent measured <= 3e-7)
         assert rel(r.p0, p) < tol, (pr.n, pr.kernel, rel(r.p0, p))
         assert abs(r.resid - resid) < tol * resid
         assert abs(r.H - o.hamiltonian(pr.X, p, pr.kernel, pr.sigma)) < 10 * tol * abs(r.H)
@@ -72,7 +72,7 @@ def test_batched_default_gain_convergence_and_host_arrays():
         assert abs(r.h - o.default_gain(pr.X, pr.kernel, pr.sigma)) < 1e-6 * r.h
         p, st, it, resid, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=r.h, eps=5e-3, maxit=60)
         assert r.status == st and r.iters == it
-        assert rel(r.p0, p) < 1e-3
+        assert rel(r.p0, p) < 1e-4
 
 
 def test_batched_matches_single_problem_path():
@@ -100,7 +100,7 @@ def test_batched_full_workload_sampled():
         pr = prs[b]
         p, st, it, resid, hist = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=res[b].h, eps=1e-12,
                                          maxit=2)
-        tol = 1e-3 if pr.kernel == ep.TENT else 1e-4
+        tol = 1e-4  # both kernels (tent measured <= 3e-7)
         assert rel(res[b].p0, p) < tol
 
 
@@ -109,3 +109,43 @@ def test_batched_invalid_sizes():
     with pytest.raises(ep.EPError):
         ep.match_batched(X, X, [ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=2)], maxit=1)
     assert ep.match_batched([], [], []) == []
+
+
+def test_batched_per_problem_status_through_the_c_abi():
+    """ep_match_batched reports each problem's own status in infos[b].status (Algorithm 1
+    steps 2-3, decided on the device): one problem converges, one stops at the cap, one
+    diverges under too large a gain; the oracle agrees on each."""
+    import ctypes
+
+    prs = problems([48, 64, 80], steps=5)
+    hs = [0.0, 0.002, 60.0]  # default gain; a gain too small to converge in maxit; divergence
+    eps, maxit = 2e-2, 40
+    offs = np.zeros(len(prs) + 1, dtype=np.int64)
+    for b, pr in enumerate(prs):
+        offs[b + 1] = offs[b] + pr.n
+    X = torch.tensor(np.concatenate([p.X for p in prs]), device="cuda")
+    Y = torch.tensor(np.concatenate([p.Y for p in prs]), device="cuda")
+    p0 = torch.zeros_like(X)
+    P = (ep.Params * 3)(*[ep.params(dim=2, kernel=p.kernel, sigma=p.sigma, steps=p.steps, precision=ep.MIXED,
+                                     neigh=ep.ALLPAIRS) for p in prs])
+    infos = (ep.MatchInfo * 3)(*[ep.MatchInfo(hs[b], eps, maxit, 0, 0.0, 0.0, None) for b in range(3)])
+    for b in range(3):
+        infos[b].status = -1
+    lib = ep.load()
+    st = lib.ep_match_batched(P, 3, offs.ctypes.data, X.data_ptr(), Y.data_ptr(), p0.data_ptr(), infos,
+                              torch.cuda.current_stream().cuda_stream)
+    statuses = [infos[b].status for b in range(3)]
+    ref = []
+    for b, pr in enumerate(prs):
+        h = infos[b].h
+        _, s_ref, it, _, _ = o.match(pr.X, pr.Y, pr.kernel, pr.sigma, pr.steps, h=h, eps=eps, maxit=maxit)
+        ref.append(s_ref)
+        if s_ref != ep.EDIVERGED:
+            assert infos[b].iters == it
+    assert statuses == ref == [ep.OK, ep.ENOTCONVERGED, ep.EDIVERGED]
+    assert st == ep.ENOTCONVERGED  # the first non-OK status in problem order
+    res = ep.match_batched([torch.tensor(p.X, device="cuda") for p in prs],
+                           [torch.tensor(p.Y, device="cuda") for p in prs],
+                           [ep.params(dim=2, kernel=p.kernel, sigma=p.sigma, steps=p.steps, precision=ep.MIXED)
+                            for p in prs], h=hs, eps=eps, maxit=maxit)
+    assert [r.status for r in res] == statuses

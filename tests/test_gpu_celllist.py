@@ -1,7 +1,7 @@
 """GPU cell list (tent kernel, 2-D): neighbour sets bit-exact against the oracle's
 brute force of the same predicate, and RHS / shoot / match parity with the FP64
-oracle (mixed precision: RHS <= 1e-5, endpoints <= 1e-3 because of the tent's
-jump at r = sigma), through the C ABI.  At the full 512 x 512 jittered-grid size
+oracle (mixed precision: RHS <= 1e-5 away from the tent's jump at r = sigma,
+endpoints <= 1e-4), through the C ABI.  At the full 512 x 512 jittered-grid size
 the oracle checks a sample of rows."""
 import numpy as np
 import pytest
@@ -114,13 +114,13 @@ def test_shoot_and_match_parity():
     prm = ep.params(dim=2, kernel=ep.TENT, sigma=pr.sigma, steps=6, precision=ep.MIXED, neigh=ep.CELLLIST)
     q1, p1 = ep.shoot(cuda(pr.X), cuda(p), prm)
     rq, rp = o.shoot(pr.X, p, ep.TENT, pr.sigma, 6)
-    assert rel(q1, rq) < 1e-3 and rel(p1, rp) < 1e-3
+    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
     assert np.abs(q1.cpu().numpy() - rq).max() < 1e-6
     r = ep.match(cuda(pr.X), cuda(pr.Y), prm, h=0.02, eps=1e-9, maxit=4)
     pm, st, it, res, hist = o.match(pr.X, pr.Y, ep.TENT, pr.sigma, 6, h=0.02, eps=1e-9, maxit=4)
     assert r.iters == it
-    assert rel(r.p0, pm) < 1e-3
-    np.testing.assert_allclose(r.hist, hist, rtol=1e-3)
+    assert rel(r.p0, pm) < 1e-4
+    np.testing.assert_allclose(r.hist, hist, rtol=1e-4)
 
 
 def test_cell_list_is_deterministic():
@@ -140,7 +140,7 @@ def test_shoot_with_large_motion():
     q1, p1 = ep.shoot(cuda(pr.X), cuda(p), prm)
     rq, rp = o.shoot(pr.X, p, ep.TENT, pr.sigma, 20)
     assert np.abs(rq - pr.X).max() > 1.2 * pr.sigma
-    assert rel(q1, rq) < 1e-3 and rel(p1, rp) < 1e-3
+    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
 
 
 def test_dense_cluster_beyond_the_staging_capacity():
@@ -154,4 +154,4 @@ def test_dense_cluster_beyond_the_staging_capacity():
     prm = ep.params(dim=2, kernel=ep.TENT, sigma=sigma, steps=4, precision=ep.MIXED, neigh=ep.CELLLIST)
     q1, p1 = ep.shoot(cuda(X), cuda(p), prm)
     rq, rp = o.shoot(X, p, ep.TENT, sigma, 4)
-    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-3
+    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
