@@ -609,9 +609,9 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True) ->
                                          "h=0.5, velocity update h G(X)^-1 r",
                              "seconds_per_match": dt, "matchings_per_s": 1.0 / dt, "iters": r.iters, "status": r.status,
                              "resid": r.resid, "krylov_products": r.products,
-                             "roofline": {"bound": "latency", "note": f"{r.iters} updates, each a mixed persistent shoot, "
-                                          "an FP64 residual and one warp's substitutions with the factored G(X); "
-                                          "the oracle's time is the velocity_fp64 row's"}}
+                             "roofline": {"bound": "latency", "note": f"one launch on one CTA: {r.iters + 1} mixed shoots, FP64 "
+                                          "residuals and {r.iters} FP64 updates p0 += h G(X)^-1 r (G(X)^-1 formed "
+                                          "once from its LU factors); the oracle's time is the velocity_fp64 row's"}}
     if with_cpu:
         def run_small(o):
             _, _, it, _, _ = o.match(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.0, eps=c.eps, maxit=c.maxit)

@@ -58,6 +58,7 @@ struct BProb {
     double s;        // coordinate scale
     double dp_scale;
     double* hist;    // optional device array (maxit + 1): residual of every shoot
+    const double* ginv;  // G(X)^-1 (n x n, row-major, FP64): velocity update (solo problems); null: momentum rule
 };
 
 struct BOut {
@@ -413,9 +414,22 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
         if (bad > 0.0) { status = EP_EDIVERGED; break; }
         if (res < P.eps) { status = EP_OK; break; }
         if (k == P.maxit) { status = EP_ENOTCONVERGED; break; }
-        // p0 += h (Y - Q(1))   (FP64)
-        for (int i = lo + threadIdx.x; i < hi; i += kThreads)
-            for (int c = 0; c < 2; ++c) p0[2 * i + c] = fma(h, Y[2 * i + c] - xs[4 * i + c], p0[2 * i + c]);
+        if (P.ginv) {
+            // velocity update (Algorithm 1 steps 3-4): u0 = G(X) p0 gains h (Y - Q(1)) and
+            // p0 = G(X)^-1 u0, i.e. p0 += h G(X)^-1 (Y - Q(1)); one thread per (row, component),
+            // FP64 (a solo problem: this CTA holds every Q(1))
+            for (int e = threadIdx.x; e < 2 * n; e += kThreads) {
+                const int i = e >> 1, c = e & 1;
+                const double* g = P.ginv + (size_t)i * n;
+                double sdl = 0.0;
+                for (int j = 0; j < n; ++j) sdl = fma(g[j], Y[2 * j + c] - xs[4 * j + c], sdl);
+                p0[e] = fma(h, sdl, p0[e]);
+            }
+        } else {
+            // p0 += h (Y - Q(1))   (FP64)
+            for (int i = lo + threadIdx.x; i < hi; i += kThreads)
+                for (int c = 0; c < 2; ++c) p0[2 * i + c] = fma(h, Y[2 * i + c] - xs[4 * i + c], p0[2 * i + c]);
+        }
         ++k;
         team_sync(t);  // p0 of every slice written before the next shoot reads it
     }
@@ -489,7 +503,8 @@ bool is_dev(const void* p)
 }  // namespace
 
 ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets, const double* X, const double* Y,
-                      double* p0, ep_match_info* infos, void* stream, double* const* hist_dev);
+                      double* p0, ep_match_info* infos, void* stream, double* const* hist_dev,
+                      const double* const* ginv = nullptr);
 
 
 ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offsets, const double* X,
@@ -500,7 +515,7 @@ ep_status batched_entry(const ep_params* params, int nprob, const int64_t* offse
 
 // ep_match of one small 2-D mixed-precision problem on one CTA (the batched solver).
 ep_status match_small(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
-                      ep_match_info* info, void* stream)
+                      ep_match_info* info, void* stream, const double* ginv)
 {
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t offsets[2] = {0, n};
@@ -514,7 +529,7 @@ ep_status match_small(const ep_params* params, int64_t n, const double* X, const
             EP_TRY_CUDA(cudaMallocAsync(&hdev, sizeof(double) * (info->maxit + 1), st));
         }
     }
-    ep_status s = batched_run(params, 1, offsets, X, Y, p0, info, stream, &hdev);
+    ep_status s = batched_run(params, 1, offsets, X, Y, p0, info, stream, &hdev, ginv ? &ginv : nullptr);
     if (hist_host) {
         EP_TRY_CUDA(cudaMemcpyAsync(info->hist, hdev, sizeof(double) * (info->iters + 1), cudaMemcpyDeviceToHost, st));
         EP_TRY_CUDA(cudaFreeAsync(hdev, st));
@@ -525,7 +540,8 @@ ep_status match_small(const ep_params* params, int64_t n, const double* X, const
 
 
 ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets, const double* X, const double* Y,
-                      double* p0, ep_match_info* infos, void* stream, double* const* hist_dev)
+                      double* p0, ep_match_info* infos, void* stream, double* const* hist_dev,
+                      const double* const* ginv)
 {
     if (nprob < 0) return set_error("ep_match_batched: nprob < 0"), EP_EINVAL;
     if (nprob == 0) return EP_OK;
@@ -548,8 +564,10 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
             return set_error("ep_match_batched: internal size limit"), EP_EINVAL;
         const ep_match_info& I = infos[b];
         if (I.maxit < 0 || !(I.eps >= 0.0)) return set_error("ep_match_batched: problem %d: bad maxit/eps", b), EP_EINVAL;
-        if (I.rule != EP_RULE_MOMENTUM)
+        const bool vel = ginv && ginv[b];
+        if (I.rule != (vel ? EP_RULE_VELOCITY : EP_RULE_MOMENTUM))
             return set_error("ep_match_batched: problem %d: only the momentum update rule is batched", b), EP_EINVAL;
+        if (vel && nb >= team_min) return set_error("ep_match: internal size limit (velocity update)"), EP_EINVAL;
         const KernelScale ks = kernel_scale(P.kernel, P.sigma);
         BProb& q = probs[b];
         q.off = offsets[b];
@@ -564,6 +582,7 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
         q.s = ks.s;
         q.dp_scale = ks.dp_scale;
         q.hist = hist_dev ? hist_dev[b] : nullptr;
+        q.ginv = vel ? ginv[b] : nullptr;
     }
     const int64_t ntot = offsets[nprob];
     // order: team problems then solo problems, each by decreasing n^2 (LPT)

@@ -36,8 +36,10 @@ ep_status velocity_entry(const ep_params* params, int64_t n, const double* q, co
 ep_status flow_entry(const ep_params* params, int64_t n, const double* q0, const double* p0, int64_t m,
                      const double* x0, double* x1, void* stream);
 // ep_match of one small 2-D mixed-precision problem, solved entirely on one CTA.
+// ginv (device, n x n row-major, or null): G(X)^-1 for the velocity update
+// p0 += h G(X)^-1 (Y - Q(1)); null runs the momentum rule.
 ep_status match_small(const ep_params* params, int64_t n, const double* X, const double* Y, double* p0,
-                      ep_match_info* info, void* stream);
+                      ep_match_info* info, void* stream, const double* ginv = nullptr);
 
 // Algorithm 1 for the plain FP64 method in one cooperative launch (ep_match_dev.cu):
 // X, Y, p0 device arrays (p0 in/out), hist_dev maxit + 1 doubles on the device or

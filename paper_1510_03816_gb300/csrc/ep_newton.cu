@@ -632,6 +632,18 @@ __global__ void k_gram_solve(int n, int dim, const double* Gm, const int* piv, c
     }
 }
 
+// G(X)^-1 from its LU factors, one column per CTA (one warp: the substitutions of
+// LU x = P e_c); Ginv row-major (n x n).  n <= kSmallMatchMaxN (shared scratch).
+__global__ void k_lu_inverse(int n, const double* __restrict__ LU, const int* __restrict__ piv, double* __restrict__ Ginv)
+{
+    __shared__ double b[kSmallMatchMaxN];
+    const int c = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += 32) b[i] = i == c ? 1.0 : 0.0;
+    __syncwarp();
+    warp_lu_solve(n, LU, piv, b);
+    for (int i = threadIdx.x; i < n; i += 32) Ginv[(size_t)i * n + c] = b[i];
+}
+
 // Device buffers of one tangent-linear problem.
 struct TanBufs {
     AllPairsBufs ap;
@@ -1110,6 +1122,7 @@ ep_status velocity_mixed_match(const ep_params& P, int64_t n, const double* X, c
     z.add(sizeof(int) * (size_t)n);
     for (int k = 0; k < 7; ++k) z.add(sizeof(double) * m);
     z.add(64);
+    z.add(sizeof(double) * (size_t)n * n);  // G(X)^-1 (small planar problems)
     Arena* ar = nullptr;
     EP_TRY(arena_acquire(st, z.total, &ar));
     AllPairsBufs ap;
@@ -1148,6 +1161,29 @@ ep_status velocity_mixed_match(const ep_params& P, int64_t n, const double* X, c
     EP_TRY_CUDA(cudaMemcpyAsync(&ok, dok, sizeof(int), cudaMemcpyDeviceToHost, st));
     EP_TRY_CUDA(cudaStreamSynchronize(st));
     if (!ok) return set_error("ep_match: G(X) is singular (the velocity update needs G(X)^-1)"), EP_EDIVERGED;
+    if (P.dim == 2 && n <= kSmallMatchMaxN) {
+        // small planar problems: G(X)^-1 formed once, then the whole feedback loop (mixed
+        // shoots, FP64 residual, FP64 update p0 += h G(X)^-1 r) in one launch on one CTA
+        double* Ginv = (double*)ar->carve(sizeof(double) * (size_t)n * n);
+        if (!Ginv) return set_error("ep_match: workspace too small"), EP_ENOMEM;
+        count_launch();
+        k_lu_inverse<<<(unsigned)n, 32, 0, st>>>((int)n, Gm, piv, Ginv);
+        EP_TRY_CUDA(cudaGetLastError());
+        ep_params Pv = P;
+        ep_match_info iv = *info;
+        const ep_status s = match_small(&Pv, n, dX, dY, dp, &iv, st, Ginv);
+        if (s != EP_OK && s != EP_ENOTCONVERGED && s != EP_EDIVERGED) return s;
+        info->iters = iv.iters;
+        info->resid_inf = iv.resid_inf;
+        info->H = iv.H;
+        info->products = P.dim * iv.iters;
+        EP_TRY_CUDA(cudaMemcpyAsync(p0, dp, sizeof(double) * m, cudaMemcpyDefault, st));
+        EP_TRY_CUDA(cudaStreamSynchronize(st));
+        if (s == EP_ENOTCONVERGED)
+            set_error("ep_match: %d iterations, residual %.3e >= eps %.3e", iv.iters, iv.resid_inf, info->eps);
+        if (s == EP_EDIVERGED) set_error("ep_match: residual became non-finite after %d updates", iv.iters);
+        return s;
+    }
     ep_status status = EP_ENOTCONVERGED;
     int k = 0;
     double res = 0.0;

@@ -131,3 +131,33 @@ def test_adjoint_full_size_star_surface_directional_fd():
     fd = (Ep - Em) / (2 * h)
     dd = float((g * v).sum())
     assert abs(fd - dd) < 2e-3 * abs(dd)
+
+
+def test_adjoint_full_size_star_surface_fp64_central_differences():
+    """The gradient check of the inexact-matching energy at its stated size (Sec. 6,
+    Eq. inexact-E): N = 16384 3-D, Gaussian sigma = 0.05, lambda = 100, 100 RK4 steps,
+    checkpoints every 10, FP64.  <dE/dp0, v> from the discrete adjoint against the
+    central difference (E(p0 + h v) - E(p0 - h v)) / 2h with h = 1e-4, every energy in
+    FP64 (1/2 p0^T G(X) p0 = H(X, p0) of Eq. H, plus lambda/2 |Q(1) - Y|^2 from the plain
+    FP64 shoot); the O(h^2) truncation leaves ~1e-8 of the derivative.  The mixed-
+    precision gradient agrees with the FP64 one to the adjoint's mixed bound."""
+    pr = w.star_surface_3d()
+    X, Y, p0 = cuda(pr.X), cuda(pr.Y), cuda(pr.p0)
+    prm = ep.params(dim=3, kernel=pr.kernel, sigma=pr.sigma, steps=pr.steps, precision=ep.FP64)
+    E, g = ep.adjoint(X, p0, Y, prm, pr.lam, ckpt_every=10)
+
+    def energy(p):
+        q1, _ = ep.shoot(X, p, prm)
+        return ep.hamiltonian(X, p, prm) + 0.5 * pr.lam * float(((q1 - Y) ** 2).sum())
+
+    assert abs(energy(p0) - E) < 1e-11 * abs(E)
+    v = cuda(np.random.default_rng(17).normal(size=pr.p0.shape))
+    v = v / v.norm() * p0.norm()
+    h = 1e-4
+    fd = (energy(p0 + h * v) - energy(p0 - h * v)) / (2 * h)
+    dd = float((g * v).sum())
+    assert abs(fd - dd) < 1e-6 * abs(dd)
+    prm_m = ep.params(dim=3, kernel=pr.kernel, sigma=pr.sigma, steps=pr.steps, precision=ep.MIXED)
+    Em, gm = ep.adjoint(X, p0, Y, prm_m, pr.lam, ckpt_every=10)
+    assert rel(gm, g.cpu().numpy()) < 1e-3
+    assert abs(Em - E) < 1e-4 * abs(E)

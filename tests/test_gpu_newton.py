@@ -460,3 +460,18 @@ def test_velocity_rule_mixed_bench_workload():
     rp, st, it, r, hist = o.match_velocity(c.X, c.Y, c.kernel, c.sigma, c.steps, h=0.5, eps=c.eps, maxit=c.maxit)
     assert res.status == st == ep.OK and abs(res.iters - it) <= 1
     assert rel(res.p0, rp) < 1e-4
+
+
+@pytest.mark.parametrize("dim,n", [(3, 24), (2, 400)])
+def test_velocity_rule_mixed_host_loop(dim, n):
+    # beyond the one-launch solver (3-D, or planar n > 384): mixed persistent shoots and
+    # one warp's substitutions with the factored G(X) per update, on the host loop
+    sigma = 0.08 if dim == 3 else 0.03
+    X, _ = cloud(n, dim, seed=31 + dim, sigma=sigma, band=1e-4)
+    Y = X + 0.002 * np.random.default_rng(32).normal(size=X.shape)
+    prm = ep.params(dim=dim, kernel=ep.TENT, sigma=sigma, steps=6, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    res = _match(X, Y, prm, ep.RULE_VELOCITY, h=0.5, eps=0.0, maxit=3)
+    rp, st, it, r, hist = o.match_velocity(X, Y, ep.TENT, sigma, 6, h=0.5, eps=0.0, maxit=3)
+    assert res.iters == it == 3 and res.products == 3 * dim
+    assert rel(res.p0, rp) < 1e-4
+    np.testing.assert_allclose(res.hist, hist, rtol=1e-4)
