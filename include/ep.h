@@ -268,10 +268,12 @@ int ep_version(void);
 
 /* Launch timing of the persistent all-pairs shoot (the fused RK4 integration of
  * Sec. 4; one cooperative launch per ep_shoot and per feedback iterate of
- * ep_match).  With timing on, CUDA events are recorded on the caller's stream
- * around that launch: ep_last_launch_ms() returns the duration of the last timed
- * launch in milliseconds (-1 if none) and ep_last_launch_kernel() the name of its
- * kernel ("" if none).  Off by default; the setting is process-wide. */
+ * ep_match) and of the persistent batched launch of ep_match_batched.  With timing
+ * on, CUDA events are recorded on the caller's stream around that launch:
+ * ep_last_launch_ms() returns the duration of the last timed launch in
+ * milliseconds (-1 if none) and ep_last_launch_kernel() the name of its kernel and
+ * launch shape ("" if none; for the batched launch the autotuned cluster size,
+ * team threshold and lanes per particle).  Off by default; process-wide. */
 void ep_set_launch_timing(int on);
 double ep_last_launch_ms(void);
 const char* ep_last_launch_kernel(void);

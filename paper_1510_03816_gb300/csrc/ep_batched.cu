@@ -3,7 +3,7 @@
 //
 // Work distribution.  Problems are ordered by decreasing cost (n^2, longest
 // processing time first) and handed out through two global counters.  The
-// launch is a grid of thread-block clusters of kCluster CTAs, sized to what can
+// launch is a grid of thread-block clusters of C CTAs, sized to what can
 // be resident at once, so no CTA ever waits for one that is not running:
 //   - "team" problems (n >= team_min): all CTAs of a cluster solve one problem
 //     together.  CTA r owns the particle slice [r n / C, (r+1) n / C); every
@@ -18,11 +18,18 @@
 // per-particle sums over runs of kFold sources added in FP64 when there are several), the FP64 max-norm
 // residual, the FP64 momentum update, and finally H(X, p0) (Eq. H).
 //
+// Launch shape.  The cluster size, the team threshold team_min and the most lanes
+// sharing one particle's source loop are chosen per batch by an autotuner that
+// times a short trial of the batch itself with each valid shape (batched_tune) and
+// caches the fastest for the batch's size signature.
+//
 // Scaled coordinates as in the all-pairs path: q' = s (q - c0), c0 the centre of
 // the bounding box of X, s and the momentum factor dp_scale from the kernel.
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -31,6 +38,7 @@
 #include <numeric>
 #include <vector>
 
+#include "ep_allpairs.cuh"
 #include "ep_features.cuh"
 
 namespace cg = cooperative_groups;
@@ -39,7 +47,7 @@ namespace ep {
 
 namespace {
 
-constexpr int kCluster = 4;
+constexpr int kCluster = 4;          // default cluster size (the autotuner may pick another)
 constexpr int kThreads = 1024;
 constexpr int kMaxN = 8192;          // particles per problem (shared-memory records)
 constexpr int kMaxPerThread = 2;     // particles i per thread and CTA slice
@@ -81,6 +89,7 @@ struct BArgs {
     double* p0;
     double* xs;         // FP64 step state, 4 doubles per particle: (qx, qy, px, py)
     float* acc;         // FP32 RK4 accumulator, 4 floats per particle
+    int lmax;           // most lanes that share one particle's source loop (a power of two <= 32)
 };
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -303,7 +312,7 @@ __device__ void solve(const BArgs& a, int b, const Team& t, float4* rec, double*
     }
     const float s_f = (float)P.s, dps = (float)P.dp_scale;
     int L = 1;
-    while (L < 32 && (hi - lo) * 2 * L <= kThreads) L *= 2;
+    while (L < a.lmax && (hi - lo) * 2 * L <= kThreads) L *= 2;
     const bool lead = ((int)threadIdx.x % L) == 0;  // the lane that finishes its particle
 
     // centre of the bounding box of X (every CTA computes it)
@@ -539,6 +548,210 @@ ep_status match_small(const ep_params* params, int64_t n, const double* X, const
 }
 
 
+// ------------------------------------------------------------------ launch shapes and their autotuner
+// The free parameters of the batched launch: the cluster size C (the CTAs that solve
+// one team problem together, and the grid granularity), the size team_min from which
+// a problem is a team problem, and the most lanes lmax that share one particle's
+// source loop (a solo slice of m particles gets the largest L <= lmax with
+// 2 m L <= kThreads).  A team problem's slice must fit one CTA (n / C <= 2048) and so
+// must a solo problem (n < team_min <= 2048).
+struct BTune {
+    int cluster = kCluster;
+    int team_min = 2048;
+    int lmax = 32;
+    bool operator==(const BTune& o) const
+    {
+        return cluster == o.cluster && team_min == o.team_min && lmax == o.lmax;
+    }
+};
+
+bool tune_valid(const BTune& c, const std::vector<BProb>& probs)
+{
+    for (const BProb& q : probs) {
+        if (q.ginv && q.n >= c.team_min) return false;  // the velocity update is solo only
+        if (q.n >= c.team_min && (q.n + c.cluster - 1) / c.cluster > kThreads * kMaxPerThread) return false;
+    }
+    return c.team_min <= kThreads * kMaxPerThread + 1;
+}
+
+// Problem order for team_min: team problems, then solo problems, each by decreasing n^2
+// (longest processing time first).  Returns the number of team problems.
+int batch_order(const std::vector<BProb>& probs, int team_min, std::vector<int>* order)
+{
+    std::vector<int> team, solo;
+    for (int b = 0; b < (int)probs.size(); ++b) (probs[b].n >= team_min ? team : solo).push_back(b);
+    auto by_cost = [&](int x, int y) { return probs[x].n > probs[y].n || (probs[x].n == probs[y].n && x < y); };
+    std::sort(team.begin(), team.end(), by_cost);
+    std::sort(solo.begin(), solo.end(), by_cost);
+    *order = team;
+    order->insert(order->end(), solo.begin(), solo.end());
+    return (int)team.size();
+}
+
+// One launch of the persistent kernel with shape c on stream st: the problems (probs)
+// and the order are uploaded into dprobs / dorder, then the launch (counter reset +
+// kernel) runs as a CUDA graph, captured on a library stream and replayed on st; it
+// is rebuilt only when the arguments or the shape change.  Events e0 / e1, when
+// given, bracket the graph launch.
+ep_status batched_launch(const BTune& c, BArgs a, const std::vector<BProb>& probs, BProb* dprobs, int* dorder,
+                         cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> resident;  // (device, cluster size) -> resident clusters
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    std::vector<int> order;
+    a.nteam = batch_order(probs, c.team_min, &order);
+    a.lmax = c.lmax;
+    a.probs = dprobs;
+    a.order = dorder;
+    const int nprob = (int)probs.size();
+    EP_TRY_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
+    const size_t smem = sizeof(float4) * kMaxN;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attrs[1];
+    attrs[0].id = cudaLaunchAttributeClusterDimension;
+    attrs[0].val.clusterDim.x = (unsigned)c.cluster;
+    attrs[0].val.clusterDim.y = 1;
+    attrs[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    {
+        auto it = resident.find({di.device, c.cluster});
+        if (it == resident.end()) {
+            EP_TRY_CUDA(cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (c.cluster > 8)
+                EP_TRY_CUDA(cudaFuncSetAttribute(k_batched, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            cfg.gridDim = dim3((unsigned)(di.sm_count / c.cluster * c.cluster));
+            EP_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_batched, &cfg));
+            resident[{di.device, c.cluster}] = nclusters;
+        } else {
+            nclusters = it->second;
+        }
+    }
+    if (nclusters < 1) return set_error("ep_match_batched: no cluster of %d CTAs fits", c.cluster), EP_ECUDA;
+    cfg.gridDim = dim3((unsigned)(nclusters * c.cluster));
+    struct GraphCache {
+        cudaStream_t cap = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        BArgs args{};
+        unsigned grid = 0;
+        int cluster = 0;
+    };
+    static std::map<std::pair<int, cudaStream_t>, GraphCache> graphs;
+    GraphCache& gc = graphs[{di.device, st}];
+    if (!gc.exec || memcmp(&gc.args, &a, sizeof a) != 0 || gc.grid != cfg.gridDim.x || gc.cluster != c.cluster) {
+        if (gc.exec) {
+            EP_TRY_CUDA(cudaStreamSynchronize(st));
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+        }
+        if (!gc.cap) EP_TRY_CUDA(cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        EP_TRY_CUDA(cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(a.ctr, 0, sizeof(int) * 4, gc.cap);
+        cfg.stream = gc.cap;
+        cudaLaunchKernelEx(&cfg, k_batched, a);
+        EP_TRY_CUDA(cudaStreamEndCapture(gc.cap, &graph));
+        cudaError_t e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batched launch)");
+        gc.args = a;
+        gc.grid = cfg.gridDim.x;
+        gc.cluster = c.cluster;
+    }
+    count_launch();
+    if (e0) EP_TRY_CUDA(cudaEventRecord(e0, st));
+    EP_TRY_CUDA(cudaGraphLaunch(gc.exec, st));
+    if (e1) EP_TRY_CUDA(cudaEventRecord(e1, st));
+    return EP_OK;
+}
+
+// Key of a tuned shape: the batch's size signature on a device.
+struct BTuneKey {
+    int dev, nprob, nmax, ntent;
+    long long n2;
+    bool operator<(const BTuneKey& o) const
+    {
+        if (dev != o.dev) return dev < o.dev;
+        if (nprob != o.nprob) return nprob < o.nprob;
+        if (nmax != o.nmax) return nmax < o.nmax;
+        if (ntent != o.ntent) return ntent < o.ntent;
+        return n2 < o.n2;
+    }
+};
+std::mutex g_btune_mu;
+std::map<BTuneKey, BTune> g_btuned;
+
+bool batched_autotune_enabled()
+{
+    const char* e = getenv("EP_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+// The autotuner: each valid candidate shape runs a short trial of the same batch (one
+// shoot per problem, at most kTuneSteps RK4 steps, momenta copied to scratch so the
+// caller's are untouched), timed with CUDA events (best of two after one untimed
+// run); the fastest shape is cached for the batch's size signature.
+constexpr int kTuneSteps = 4;
+ep_status batched_tune(const BArgs& a0, const std::vector<BProb>& probs, BProb* dprobs, int* dorder,
+                       double* p_scratch, size_t m, cudaStream_t st, BTune* best)
+{
+    std::vector<BProb> trial(probs);
+    for (BProb& q : trial) {
+        q.maxit = 0;
+        q.steps = std::min(q.steps, kTuneSteps);
+        q.hist = nullptr;
+    }
+    BArgs a = a0;
+    a.p0 = p_scratch;
+    std::vector<BTune> cand;
+    for (int C : {4, 8, 2})
+        for (int tm : {2048, 1024})
+            for (int lm : {32, 8}) {
+                BTune c;
+                c.cluster = C;
+                c.team_min = tm;
+                c.lmax = lm;
+                if (tune_valid(c, probs)) cand.push_back(c);
+            }
+    cudaEvent_t e0, e1;
+    EP_TRY_CUDA(cudaEventCreate(&e0));
+    EP_TRY_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    ep_status out = EP_OK;
+    for (const BTune& c : cand) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && out == EP_OK; ++rep) {
+            out = cudaMemcpyAsync(p_scratch, a0.p0, sizeof(double) * m, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                      ? batched_launch(c, a, trial, dprobs, dorder, st, e0, e1)
+                      : EP_ECUDA;
+            if (out != EP_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { out = EP_ECUDA; break; }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);
+        }
+        if (out != EP_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return out;
+}
+
+// The shape a batch runs with (tuned once per size signature; defaults with
+// EP_AUTOTUNE=0 or for a single problem); the last choice is readable for reporting.
+BTune g_last_btune;
+
 ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets, const double* X, const double* Y,
                       double* p0, ep_match_info* infos, void* stream, double* const* hist_dev,
                       const double* const* ginv)
@@ -547,7 +760,6 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     if (nprob == 0) return EP_OK;
     if (!params || !offsets || !infos) return set_error("ep_match_batched: NULL argument"), EP_EINVAL;
     if (offsets[0] != 0) return set_error("ep_match_batched: offsets[0] must be 0"), EP_EINVAL;
-    const int team_min = 2048;  // problems at least this large are solved by a whole cluster
     std::vector<BProb> probs((size_t)nprob);
     for (int b = 0; b < nprob; ++b) {
         const ep_params& P = params[b];
@@ -560,14 +772,12 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
         if (nb < 0 || nb > kMaxN)
             return set_error("ep_match_batched: problem %d has n = %lld (allowed 0..%d)", b, (long long)nb, kMaxN),
                    EP_EINVAL;
-        if (nb < team_min && nb > kThreads * kMaxPerThread)
-            return set_error("ep_match_batched: internal size limit"), EP_EINVAL;
         const ep_match_info& I = infos[b];
         if (I.maxit < 0 || !(I.eps >= 0.0)) return set_error("ep_match_batched: problem %d: bad maxit/eps", b), EP_EINVAL;
         const bool vel = ginv && ginv[b];
         if (I.rule != (vel ? EP_RULE_VELOCITY : EP_RULE_MOMENTUM))
             return set_error("ep_match_batched: problem %d: only the momentum update rule is batched", b), EP_EINVAL;
-        if (vel && nb >= team_min) return set_error("ep_match: internal size limit (velocity update)"), EP_EINVAL;
+        if (vel && nb > kThreads * kMaxPerThread) return set_error("ep_match: internal size limit (velocity update)"), EP_EINVAL;
         const KernelScale ks = kernel_scale(P.kernel, P.sigma);
         BProb& q = probs[b];
         q.off = offsets[b];
@@ -585,15 +795,6 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
         q.ginv = vel ? ginv[b] : nullptr;
     }
     const int64_t ntot = offsets[nprob];
-    // order: team problems then solo problems, each by decreasing n^2 (LPT)
-    std::vector<int> team, solo;
-    for (int b = 0; b < nprob; ++b) (probs[b].n >= team_min ? team : solo).push_back(b);
-    auto by_cost = [&](int x, int y) { return probs[x].n > probs[y].n || (probs[x].n == probs[y].n && x < y); };
-    std::sort(team.begin(), team.end(), by_cost);
-    std::sort(solo.begin(), solo.end(), by_cost);
-    std::vector<int> order(team);
-    order.insert(order.end(), solo.begin(), solo.end());
-
     cudaStream_t st = (cudaStream_t)stream;
     const size_t m = 2 * (size_t)ntot;
     Sizer z;
@@ -603,7 +804,7 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     z.add(sizeof(int) * 4);
     z.add(sizeof(double) * 4 * (size_t)ntot);
     z.add(sizeof(float) * 4 * (size_t)ntot);
-    z.add(sizeof(double) * m * 3);
+    z.add(sizeof(double) * m * 4);
     Arena* ar = nullptr;
     EP_TRY(arena_acquire(st, z.total, &ar));
     BProb* dprobs = (BProb*)ar->carve(sizeof(BProb) * nprob);
@@ -631,13 +832,8 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
         if (!dp0) return set_error("ep_match_batched: workspace too small"), EP_ENOMEM;
         EP_TRY_CUDA(cudaMemcpyAsync(dp0, p0, sizeof(double) * m, cudaMemcpyHostToDevice, st));
     }
-    EP_TRY_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BProb) * nprob, cudaMemcpyHostToDevice, st));
-    EP_TRY_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int) * nprob, cudaMemcpyHostToDevice, st));
     BArgs a{};
-    a.probs = dprobs;
     a.outs = douts;
-    a.order = dorder;
-    a.nteam = (int)team.size();
     a.nprob = nprob;
     a.ctr = dctr;
     a.X = dX;
@@ -646,73 +842,54 @@ ep_status batched_run(const ep_params* params, int nprob, const int64_t* offsets
     a.xs = xs;
     a.acc = acc;
 
-    // persistent grid: as many clusters as can be resident at once
-    const size_t smem = sizeof(float4) * kMaxN;
-    static std::mutex mu;
-    static std::map<int, int> resident;  // device -> resident clusters
-    DeviceInfo di{};
-    EP_TRY(device_info(&di));
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute attrs[1];
-    attrs[0].id = cudaLaunchAttributeClusterDimension;
-    attrs[0].val.clusterDim.x = kCluster;
-    attrs[0].val.clusterDim.y = 1;
-    attrs[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.attrs = attrs;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = resident.find(di.device);
-        if (it == resident.end()) {
-            EP_TRY_CUDA(cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            cfg.gridDim = dim3((unsigned)(di.sm_count / kCluster * kCluster));
-            EP_TRY_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_batched, &cfg));
-            resident[di.device] = nclusters;
-        } else {
-            nclusters = it->second;
+    // the launch shape: tuned once per batch size signature (several problems), else defaults
+    BTune shape;
+    if (nprob > 1 && batched_autotune_enabled()) {
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        BTuneKey key{di.device, nprob, 0, 0, 0};
+        for (const BProb& q : probs) {
+            key.nmax = std::max(key.nmax, q.n);
+            key.ntent += q.kernel == EP_TENT ? 1 : 0;
+            key.n2 += (long long)q.n * q.n;
+        }
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_btune_mu);
+            auto it = g_btuned.find(key);
+            if (it != g_btuned.end()) shape = it->second, have = true;
+        }
+        if (!have) {
+            double* scratch = (double*)ar->carve(sizeof(double) * m + 8);
+            if (!scratch) return set_error("ep_match_batched: workspace too small"), EP_ENOMEM;
+            EP_TRY(batched_tune(a, probs, dprobs, dorder, scratch, m, st, &shape));
+            std::lock_guard<std::mutex> lk(g_btune_mu);
+            g_btuned[key] = shape;
         }
     }
-    if (nclusters < 1) return set_error("ep_match_batched: no cluster of %d CTAs fits", kCluster), EP_ECUDA;
-    cfg.gridDim = dim3((unsigned)(nclusters * kCluster));
-
-    // The launch (counter reset + persistent kernel) is a CUDA graph, captured on a
-    // library stream and replayed on the caller's stream; it is rebuilt only when
-    // the kernel arguments change (new buffers or sizes).
-    struct GraphCache {
-        cudaStream_t cap = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        BArgs args{};
-        unsigned grid = 0;
-    };
-    static std::map<std::pair<int, cudaStream_t>, GraphCache> graphs;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        GraphCache& gc = graphs[{di.device, st}];
-        if (!gc.exec || memcmp(&gc.args, &a, sizeof a) != 0 || gc.grid != cfg.gridDim.x) {
-            if (gc.exec) {
-                EP_TRY_CUDA(cudaStreamSynchronize(st));
-                cudaGraphExecDestroy(gc.exec);
-                gc.exec = nullptr;
-            }
-            if (!gc.cap) EP_TRY_CUDA(cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking));
-            cudaGraph_t graph = nullptr;
-            EP_TRY_CUDA(cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal));
-            cudaMemsetAsync(dctr, 0, sizeof(int) * 4, gc.cap);
-            cfg.stream = gc.cap;
-            cudaLaunchKernelEx(&cfg, k_batched, a);
-            EP_TRY_CUDA(cudaStreamEndCapture(gc.cap, &graph));
-            cudaError_t e = cudaGraphInstantiate(&gc.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batched launch)");
-            gc.args = a;
-            gc.grid = cfg.gridDim.x;
+    if (!tune_valid(shape, probs)) return set_error("ep_match_batched: no valid launch shape"), EP_EINVAL;
+    g_last_btune = shape;
+    // with launch timing on (ep_set_launch_timing), CUDA events around the graph launch;
+    // the reported name carries the launch shape
+    cudaEvent_t te0 = nullptr, te1 = nullptr;
+    if (launch_timing_enabled() && nprob > 1) {
+        if (cudaEventCreate(&te0) != cudaSuccess || cudaEventCreate(&te1) != cudaSuccess) {
+            if (te0) cudaEventDestroy(te0);
+            te0 = te1 = nullptr;
         }
-        count_launch();
-        EP_TRY_CUDA(cudaGraphLaunch(gc.exec, st));
     }
+    const ep_status ls = batched_launch(shape, a, probs, dprobs, dorder, st, te0, te1);
+    if (te0 && ls == EP_OK && cudaEventSynchronize(te1) == cudaSuccess) {
+        char name[96];
+        snprintf(name, sizeof(name), "k_batched (cluster %d, team_min %d, lmax %d)", shape.cluster, shape.team_min,
+                 shape.lmax);
+        record_launch_time(te0, te1, name);
+    }
+    if (te0) {
+        cudaEventDestroy(te0);
+        cudaEventDestroy(te1);
+    }
+    EP_TRY(ls);
 
     std::vector<BOut> outs((size_t)nprob);
     EP_TRY_CUDA(cudaMemcpyAsync(outs.data(), douts, sizeof(BOut) * nprob, cudaMemcpyDeviceToHost, st));

@@ -149,3 +149,31 @@ def test_batched_per_problem_status_through_the_c_abi():
                            [ep.params(dim=2, kernel=p.kernel, sigma=p.sigma, steps=p.steps, precision=ep.MIXED)
                             for p in prs], h=hs, eps=eps, maxit=maxit)
     assert [r.status for r in res] == statuses
+
+
+def test_batched_autotuned_shape_matches_the_default_shape():
+    """The launch shape (cluster size, team threshold, lanes per particle) is chosen by the
+    library's autotuner; whatever it picks, the matchings agree with the default shape's
+    (EP_AUTOTUNE=0) to FP32 summation-order level, and the shape is reported."""
+    import os
+
+    prs = problems([40, 300, 1100, 2100, 2500, 5000], steps=3)
+    old = os.environ.get("EP_AUTOTUNE")
+    try:
+        os.environ["EP_AUTOTUNE"] = "0"
+        ref = run_batched(prs, 0.0, eps=1e-12, maxit=2)
+        os.environ["EP_AUTOTUNE"] = "1"
+        run_batched(prs, 0.0, eps=1e-12, maxit=0)  # tunes
+        ep.set_launch_timing(True)
+        res = run_batched(prs, 0.0, eps=1e-12, maxit=2)
+        ms, shape = ep.last_launch()
+    finally:
+        ep.set_launch_timing(False)
+        if old is None:
+            os.environ.pop("EP_AUTOTUNE", None)
+        else:
+            os.environ["EP_AUTOTUNE"] = old
+    assert shape.startswith("k_batched (cluster ") and ms > 0
+    for r, s in zip(res, ref):
+        assert r.iters == s.iters == 2
+        assert rel(r.p0, s.p0.cpu().numpy()) < 1e-5
