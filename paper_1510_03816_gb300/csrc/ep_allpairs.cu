@@ -36,6 +36,10 @@ namespace ep {
 namespace {
 
 constexpr int kChunk = 2048;  // sources staged per shared-memory fill (mixed)
+// The barrier word array of the persistent shoots: [0, 8) arrival counters, [8] the
+// error flag, [kBarProgress, + kMaxPersistentCtas) one progress word per CTA.
+constexpr int kBarProgress = 16;
+constexpr int kMaxPersistentCtas = 1024;
 constexpr int kChunk64 = 1024;
 
 
@@ -173,14 +177,25 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 // needs no cross-CTA reduction: the CTA applies the RK4 stage to its own rows and
 // one grid-wide barrier per stage publishes the next stage's inputs.
 //
-// Rows are processed in sub-tiles of R = (32 / JL) x 4 particles.  A warp's lanes
-// are (32 / JL) row groups x JL source lanes; a lane holds 4 rows (row group g:
+// Rows are processed in sub-tiles of R = (32 / JL) x RI particles.  A warp's lanes
+// are (32 / JL) row groups x JL source lanes; a lane holds RI rows (row group g:
 // rows g, g + 32/JL, ...) and takes every JL-th source of its warp's share, so each
-// staged source record feeds 4 particles of the lane.  The source lanes and the
-// warps are reduced after the sub-tile: a warp's block of a particle's sum (its
-// n / W sources, at most 256 since n <= kOwnerMaxN) is FP32 (lane sums, then
-// shuffles over the source lanes); the W blocks are accumulated in double-FP32
-// (TwoSum) in shared memory, to FP64-level accuracy.
+// staged source record feeds RI particles of the lane.  Two forms: 1024 threads with
+// RI = 4 (64 registers a thread), and 512 threads with RI = 8 and JL = 8 (128
+// registers: half the shared-memory loads per pair and twice the independent ex2
+// chains per lane; the benchmark's form).
+//
+// Staging: the W warps split the n sources into equal shares, and each warp stages
+// only its own share, the sources its loop reads: their loads are issued together
+// with the sub-tile's row loads and a warp barrier (no CTA barrier) separates a
+// warp's staging from its loop.  All n <= kOwnerMaxN sources fit one staged chunk.
+// Records are three arrays (A, B float4 and the y py float), which measured faster
+// in the loop than interleaved A, B pairs.
+//
+// The source lanes and the warps are reduced after the sub-tile: a warp's block of a
+// particle's sum (its n / W sources, at most 256) is FP32 (lane sums, then shuffles
+// over the source lanes); the W blocks are accumulated in double-FP32 (TwoSum) in
+// shared memory, to FP64-level accuracy.
 //
 // Factored Gaussian on coordinates centred on the sub-tile's first particle,
 // q'' = q' - q'_first: with G = 2^-|q''_i - q''_j|^2 (scaled units),
@@ -188,7 +203,7 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 //   dq_i = E_i sum_j g_ij p_j,   M_i = q''_i (x) dq_i - E_i sum_j g_ij (q''_j (x) p_j),
 // so a pair costs two FMAs for t, one ex2 and three packed f32x2 FMAs, against
 // per-source records (2x, 2y, -|q''|^2, y px), (px, py, x px, x py), (y py) built
-// once per staged chunk.  A sub-tile whose |q''_i|^2 could overflow 2^t
+// once per stage.  A sub-tile whose |q''_i|^2 could overflow 2^t
 // (> kFactorMax) takes the difference form d = q''_i - q''_j (same records).
 constexpr int kChunkG = 2048;
 constexpr float kFactorMax = 60.0f;
@@ -261,46 +276,60 @@ __device__ __forceinline__ void epilogue2_comp(const StageArgs& a, int i, int co
     }
 }
 
-// Sources staged per shared-memory fill of the owner kernel: all of them up to
-// 4096 when the sub-tile is narrow (JL >= 4), 2048 with 128-row sub-tiles (whose
-// reduction buffer is larger).
+// Sources staged per shared-memory fill of the owner kernel (the kernel takes one
+// fill: n <= this): 4096 when the sub-tile is narrow (JL >= 4), 2048 with 128-row
+// sub-tiles (whose reduction buffer is larger).
 template <int JL>
 __host__ __device__ constexpr int owner_chunk()
 {
     return JL == 1 ? 2048 : 4096;
 }
+// Rows per lane of the owner kernel: 8 in the 512-thread form (JL = 8), else 4.
+template <int JL>
+__host__ __device__ constexpr int owner_ri()
+{
+    return JL == 8 ? 8 : 4;
+}
+template <int JL>
+__host__ __device__ constexpr int owner_threads()
+{
+    return JL == 8 ? 512 : 1024;
+}
 template <int THREADS, int JL>
 constexpr size_t owner_smem()
 {
     return (size_t)owner_chunk<JL>() * (2 * sizeof(float4) + sizeof(float)) +
-           (size_t)(THREADS / 32 + 2) * kKWidth * ((32 / JL) * 4) * sizeof(float);
+           (size_t)(THREADS / 32 + 2) * kKWidth * ((32 / JL) * owner_ri<JL>()) * sizeof(float);
 }
 
 template <int THREADS, int JL>
 __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* smem, int r0, int r1)
 {
     constexpr int W = THREADS / 32;
-    constexpr int RI = 4;
+    constexpr int RI = owner_ri<JL>();
     constexpr int RG = 32 / JL;  // row groups per warp
     constexpr int R = RG * RI;   // rows per sub-tile
     constexpr int CH = owner_chunk<JL>();
     constexpr int NV = RI * kKWidth;  // finalized partials per lane
-    float4* recA = smem;                                    // [2 * CH]
-    float* recB = reinterpret_cast<float*>(smem + 2 * CH);  // [CH]
-    float* red = recB + CH;                                 // [W][6][R]: the warps' FP32 blocks
+    constexpr int SPL = (CH / W + 31) / 32;  // staged sources per lane (a warp stages its own share)
+    float4* recA4 = smem;                                    // [CH] (2x, 2y, -|q''|^2, y px)
+    float4* recB4 = smem + CH;                               // [CH] (px, py, x px, x py)
+    float* recB = reinterpret_cast<float*>(smem + 2 * CH);   // [CH] y py
+    float* red = recB + CH;                                  // [W][6][R]: the warps' FP32 blocks
     float2* fin = reinterpret_cast<float2*>(red + (size_t)W * kKWidth * R);  // [6][R]: double-FP32 sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rg = lane / JL, jl = lane % JL;
     const int n = a.n;
     for (int t0 = r0; t0 < r1; t0 += R) {
         const int t1 = min(r1, t0 + R);
-        constexpr int PF = CH / THREADS < 2 ? CH / THREADS : 2;  // sources prefetched per thread
-        const int L0 = min(PF * THREADS, n);
-        float4 pre[PF];
+        // the warp's share of the sources, [w n / W, (w+1) n / W): its loads go out
+        // together with the sub-tile's own (n <= CH: one staged chunk)
+        const int sa = warp * n / W, sb = (warp + 1) * n / W;
+        float4 src[SPL];
 #pragma unroll
-        for (int k = 0; k < PF; ++k) {
-            const int t = threadIdx.x + k * THREADS;
-            pre[k] = t < L0 ? __ldcg(a.S_in + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < SPL; ++k) {
+            const int t = sa + lane + 32 * k;
+            src[k] = t < sb ? __ldcg(a.S_in + t) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float4 c4 = __ldcg(a.S_in + t0);  // sub-tile centre: its first particle
         float qx[RI], qy[RI];
@@ -317,23 +346,26 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
         float2 sqv[RI], sbx[RI], sby[RI];
 #pragma unroll
         for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
-        for (int cj = 0; cj < n; cj += CH) {
-            const int L = min(CH, n - cj);
-            if (cj > 0) __syncthreads();
-            for (int t = threadIdx.x; t < L; t += THREADS) {
-                const float4 v = cj == 0 && t < PF * THREADS ? pre[t / THREADS] : __ldcg(a.S_in + cj + t);
-                const float x = v.x - c4.x, y = v.y - c4.y;
-                recA[2 * t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), y * v.z);
-                recA[2 * t + 1] = make_float4(v.z, v.w, x * v.z, x * v.w);
-                recB[t] = y * v.w;
+        {
+            // the warp's records (its loop reads no others: a warp barrier suffices)
+#pragma unroll
+            for (int k = 0; k < SPL; ++k) {
+                const int t = sa + lane + 32 * k;
+                if (t < sb) {
+                    const float4 v = src[k];
+                    const float x = v.x - c4.x, y = v.y - c4.y;
+                    recA4[t] = make_float4(2.0f * x, 2.0f * y, -fmaf(x, x, y * y), y * v.z);
+                    recB4[t] = make_float4(v.z, v.w, x * v.z, x * v.w);
+                    recB[t] = y * v.w;
+                }
             }
-            __syncthreads();
-            const int ja = warp * L / W + jl, jb = (warp + 1) * L / W;
+            __syncwarp();
+            const int ja = sa + jl, jb = sb;
             if (factored) {
 #pragma unroll 2
                 for (int j = ja; j < jb; j += JL) {
                     // A = (2x, 2y, -|q''|^2, y px), B = (px, py, x px, x py), byy = y py
-                    const float4 A = recA[2 * j], B = recA[2 * j + 1];
+                    const float4 A = recA4[j], B = recB4[j];
                     const float byy = recB[j];
                     const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
                     const float2 yp = make_float2(A.w, byy);
@@ -348,7 +380,7 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
                 }
             } else {
                 for (int j = ja; j < jb; j += JL) {
-                    const float4 A = recA[2 * j], B = recA[2 * j + 1];
+                    const float4 A = recA4[j], B = recB4[j];
                     const float byy = recB[j];
                     const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
                     const float2 yp = make_float2(A.w, byy);
@@ -605,6 +637,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int n = a.n;
     const int r0 = (int)((long long)blockIdx.x * n / gridDim.x), r1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
     unsigned epoch = 0;
+    volatile unsigned* progress = bar + kBarProgress;
     a.Sx = Sx;
     const int nst = a.mode == MODE_RHS ? 1 : 4 * steps;
     for (int st = 0; st < nst; ++st) {
@@ -615,6 +648,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         a.rec_out = REC ? rec + (size_t)(st + 1) * n : nullptr;  // stage input st + 1 of a recorded shoot
         stage_owner_gauss2<THREADS, JL>(a, smem, r0, r1);
         if (st + 1 < nst && !grid_barrier(bar, err, ++epoch)) return;
+        // the CTA's progress word: the last stage it has started (read when a barrier wait
+        // gives up).  Written right after the barrier: measured ~1 us per stage faster on
+        // GB300 than the same kernel without this store.
+        if (threadIdx.x == 0) progress[blockIdx.x] = (unsigned)(st + 1);
     }
 }
 
@@ -638,6 +675,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int n = a.n;
     const int i0 = (int)((long long)blockIdx.x * n / gridDim.x), i1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
     unsigned epoch = 0;
+    volatile unsigned* progress = bar + kBarProgress;
     a.Sx = Sx;
     for (int s = 0; s < steps; ++s) {
         for (int stage = 0; stage < 4; ++stage) {
@@ -650,6 +688,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<DIM>(a, i);
             if (s == steps - 1 && stage == 3) break;
             if (!grid_barrier(bar, err, ++epoch)) return;
+            if (threadIdx.x == 0) progress[blockIdx.x] = (unsigned)(4 * s + stage + 1);  // the stage it starts
         }
     }
 }
@@ -666,6 +705,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int n = a.n;
     const int i0 = (int)((long long)blockIdx.x * n / gridDim.x), i1 = (int)((long long)(blockIdx.x + 1) * n / gridDim.x);
     unsigned epoch = 0;
+    volatile unsigned* progress = bar + kBarProgress;
     a.Sx = Sx;
     for (int s = 0; s < steps; ++s) {
         for (int stage = 0; stage < 4; ++stage) {
@@ -678,6 +718,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = i0 + threadIdx.x; i < i1; i += THREADS) epilogue_mixed<2>(a, i);
             if (s == steps - 1 && stage == 3) break;
             if (!grid_barrier(bar, err, ++epoch)) return;
+            if (threadIdx.x == 0) progress[blockIdx.x] = (unsigned)(4 * s + stage + 1);  // the stage it starts
         }
     }
 }
@@ -1001,7 +1042,7 @@ size_t allpairs_bytes(int n, int dim, int prec)
     z.add(sizeof(double) * kKWidth * (size_t)n);   // K
     z.add(sizeof(int) * (size_t)ntiles);           // counters
     z.add(sizeof(double) * 4);                     // c0
-    z.add(sizeof(unsigned) * 12);                  // barrier counters, error flag
+    z.add(sizeof(unsigned) * (kBarProgress + kMaxPersistentCtas));  // barrier counters, error flag, progress words
     if (prec == EP_MIXED && dim == 2) {
         z.add(sizeof(double) * 2 * dim * (size_t)n);  // tuner backup of x
         z.add(sizeof(float4) * (size_t)n);            // tuner backup of the stage copy
@@ -1028,7 +1069,7 @@ ep_status allpairs_carve(Arena* ar, int n, int dim, int prec, AllPairsBufs* b)
     b->K = (double*)ar->carve(sizeof(double) * kKWidth * (size_t)n);
     b->counters = (int*)ar->carve(sizeof(int) * (size_t)ntiles);
     b->c0 = (double*)ar->carve(sizeof(double) * 4);
-    b->bar = (unsigned*)ar->carve(sizeof(unsigned) * 12);
+    b->bar = (unsigned*)ar->carve(sizeof(unsigned) * (kBarProgress + kMaxPersistentCtas));
     b->err = (int*)(b->bar ? b->bar + 8 : nullptr);
     if (prec == EP_MIXED && dim == 2) {
         b->x_bak = (double*)ar->carve(sizeof(double) * 2 * dim * (size_t)n);
@@ -1116,13 +1157,23 @@ ep_status allpairs_rhs(const ep_params& P, const AllPairsBufs& b, double* dq, do
 
 // Launch of a whole persistent shoot; returns *done = false when the grid cannot
 // be co-resident (the caller then falls back to per-stage launches).
-ep_status finish_persistent(const AllPairsBufs& b, cudaStream_t st, bool* done)
+ep_status finish_persistent(const AllPairsBufs& b, cudaStream_t st, bool* done, int G = 0)
 {
     int herr = 0;
     EP_TRY_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     EP_TRY_CUDA(cudaStreamSynchronize(st));
     if (herr) {
-        set_error("persistent shoot: a grid-barrier wait gave up (kernel ended early)");
+        // the CTAs' progress words say how far each got (kernels that write them)
+        unsigned lo = 0, hi = 0;
+        if (G > 0 && G <= kMaxPersistentCtas) {
+            std::vector<unsigned> pr((size_t)G);
+            if (cudaMemcpy(pr.data(), b.bar + kBarProgress, sizeof(unsigned) * G, cudaMemcpyDeviceToHost) == cudaSuccess) {
+                lo = *std::min_element(pr.begin(), pr.end());
+                hi = *std::max_element(pr.begin(), pr.end());
+            }
+        }
+        set_error("persistent shoot: a grid-barrier wait gave up (kernel ended early; CTAs had reached stages %u..%u)",
+                  lo, hi);
         return EP_ETIMEOUT;
     }
     *done = true;
@@ -1148,7 +1199,7 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
         resident = per_sm * di.sm_count;
     }
     *done = false;
-    if (a0.G > resident) return EP_OK;  // not all CTAs can be resident: per-stage launches instead
+    if (a0.G > resident || a0.G > kMaxPersistentCtas) return EP_OK;  // per-stage launches instead
     StageArgs a = a0;
     const float4* Sx = b.Sx;
     float4* Sa = b.Sa;
@@ -1161,7 +1212,7 @@ ep_status launch_shoot_mixed(const StageArgs& a0, const AllPairsBufs& b, int ste
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
     if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
-    return finish_persistent(b, st, done);
+    return finish_persistent(b, st, done, a.G);
 }
 
 // The owner-computes 2-D Gaussian shoot: a.G CTAs, JL source lanes per row group.
@@ -1174,7 +1225,7 @@ template <int JL>
 ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cudaStream_t st, bool* done,
                        cudaEvent_t ev0, cudaEvent_t ev1, float4* rec)
 {
-    constexpr int THREADS = 1024;
+    constexpr int THREADS = owner_threads<JL>();
     const size_t smem = owner_smem<THREADS, JL>();
     auto fn = rec ? k_shoot_owner<THREADS, JL, true> : k_shoot_owner<THREADS, JL, false>;
     static int resident[2] = {-1, -1};
@@ -1190,7 +1241,7 @@ ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cu
     *done = false;
     StageArgs a = a0;
     a.G = std::max(1, std::min(a.G, a.n));
-    if (a.G > res) return EP_OK;
+    if (a.G > res || a.G > kMaxPersistentCtas || a.n > owner_chunk<JL>()) return EP_OK;  // one staged chunk holds every source
     const float4* Sx = b.Sx;
     float4* Sa = b.Sa;
     float4* Sb = b.Sb;
@@ -1202,7 +1253,7 @@ ep_status launch_owner(const StageArgs& a0, const AllPairsBufs& b, int steps, cu
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
     if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
-    return finish_persistent(b, st, done);
+    return finish_persistent(b, st, done, a.G);
 }
 
 // The stream-K 2-D Gaussian shoot over a.G CTAs (tiles of kTileG).
@@ -1227,7 +1278,7 @@ ep_status launch_streamk(const StageArgs& a0, const AllPairsBufs& b, int steps, 
     StageArgs a = a0;
     a.U = (long long)((b.n + kTileG - 1) / kTileG) * b.n;
     a.G = (int)std::max<long long>(1, std::min<long long>(a.G, a.U));
-    if (a.G > resident) return EP_OK;
+    if (a.G > resident || a.G > kMaxPersistentCtas) return EP_OK;
     const float4* Sx = b.Sx;
     float4* Sa = b.Sa;
     float4* Sb = b.Sb;
@@ -1239,7 +1290,7 @@ ep_status launch_streamk(const StageArgs& a0, const AllPairsBufs& b, int steps, 
     if (ev0) EP_TRY_CUDA(cudaEventRecord(ev0, st));
     EP_TRY_CUDA(cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st));
     if (ev1) EP_TRY_CUDA(cudaEventRecord(ev1, st));
-    return finish_persistent(b, st, done);
+    return finish_persistent(b, st, done, a.G);
 }
 
 // JL = 1, 4, 16: owner computes with that many source lanes; JL = 0: stream-K.
@@ -1251,12 +1302,13 @@ ep_status launch_owner_cfg(const StageArgs& a, const AllPairsBufs& b, int steps,
     if (c.JL == 0) return launch_streamk(a2, b, steps, st, done, ev0, ev1, rec);
     if (c.JL == 1) return launch_owner<1>(a2, b, steps, st, done, ev0, ev1, rec);
     if (c.JL == 16) return launch_owner<16>(a2, b, steps, st, done, ev0, ev1, rec);
+    if (c.JL == 8) return launch_owner<8>(a2, b, steps, st, done, ev0, ev1, rec);
     return launch_owner<4>(a2, b, steps, st, done, ev0, ev1, rec);
 }
 
-// Largest n of the owner-computes kernel: a warp's FP32 block of a particle's sum
-// covers n / 32 sources (the lane sums run over every staged chunk), at most 256.
-constexpr int kOwnerMaxN = 8192;
+// Largest n of the owner-computes kernel: every source in one staged chunk (and a
+// warp's FP32 block of a particle's sum at most n / 16 = 256 sources); stream-K above.
+constexpr int kOwnerMaxN = 4096;
 
 // Default owner configuration: the widest sub-tile the rows per SM fill, and the
 // CTA count that fills each CTA's sub-tiles; stream-K (JL = 0) beyond kOwnerMaxN.
@@ -1265,8 +1317,8 @@ OwnerCfg owner_default(int n, int sm)
     OwnerCfg c;
     if (n > kOwnerMaxN) return OwnerCfg{sm, 0};
     const double per = (double)n / sm;
-    c.JL = per >= 96 ? 1 : per >= 24 ? 4 : 16;
-    const int R = (32 / c.JL) * 4;
+    c.JL = per >= 24 ? 8 : 16;
+    const int R = (32 / c.JL) * (c.JL == 8 ? 8 : 4);
     const long long k = std::max<long long>(1, (n + (long long)sm * R - 1) / ((long long)sm * R));
     c.G = (int)std::max<long long>(1, std::min<long long>(sm, (n + k * R - 1) / (k * R)));
     return c;
@@ -1329,9 +1381,9 @@ ep_status tune_persistent(const ep_params& P, const AllPairsBufs& b, StageArgs a
         for (int k = sm / std::max(1, tiles), c = 0; k >= 1 && c < 2; --k, ++c) gs.push_back(tiles * k);
         for (int g : gs) cand.push_back(OwnerCfg{g, 0});
     } else {
-        for (int JL : {1, 4, 16}) {
-            if (n > kOwnerMaxN) break;
-            const int R = (32 / JL) * 4;
+        for (int JL : {1, 4, 8, 16}) {
+            if (n > kOwnerMaxN || (JL == 1 && n > owner_chunk<1>())) continue;
+            const int R = (32 / JL) * (JL == 8 ? 8 : 4);
             const long long k = std::max<long long>(1, (n + (long long)sm * R - 1) / ((long long)sm * R));
             const int g1 = (int)std::max<long long>(1, std::min<long long>(sm, (n + k * R - 1) / (k * R)));
             cand.push_back(OwnerCfg{g1, JL});
@@ -1449,7 +1501,7 @@ ep_status persistent_steps(const ep_params& P, const AllPairsBufs& b, StageArgs 
             if (c.JL == 0)
                 snprintf(name, sizeof(name), "k_shoot_streamk<1024> (G=%d)", c.G);
             else
-                snprintf(name, sizeof(name), "k_shoot_owner<1024,%d> (G=%d)", c.JL, std::min(c.G, b.n));
+                snprintf(name, sizeof(name), "k_shoot_owner<%d,%d> (G=%d)", c.JL == 8 ? 512 : 1024, c.JL, std::min(c.G, b.n));
         }
         if (*done) tl.record(name);
         return EP_OK;
