@@ -54,10 +54,10 @@ FLOPS_PER_PAIR_3D_HVP = 65    # one (i, j) term of the Hessian-vector product of
 FLOPS_PER_PAIR_2D_TANGENT = 58  # FP64 tangent pair: d, dd (4), r^2, d.dd, p.p (12), dp.p + p.dp (8),
                                 # phi, psi (6), dq block (10), dp block (18); exp not counted
 FP64_LANES_PER_SM = 2  # FP64 FMA per clock per SM (one warp instruction per 64 cycles per SMSP)
-# DRAM bytes (read + write) of one 400-stage launch of k_shoot_owner<1024,4> (G=128) on the
-# N = 4096 workload, from one ncu capture of that launch; None until the changed kernel is
-# captured again
-OWNER_LAUNCH_DRAM_BYTES = None
+# DRAM bytes (read + write) of one 400-stage launch of k_shoot_owner<512,8> (G=128) on the
+# N = 4096 workload, from one ncu capture of that launch; reset to None when the kernel changes
+OWNER_LAUNCH_DRAM_BYTES = 292608 + 66560
+OWNER_TRAFFIC_KERNEL = "k_shoot_owner<512,8> (G=128)"
 WORKLOAD = ("fourier_curve_warp: N=4096 2-D landmarks on a random Fourier curve -> sine warp; "
             "Gaussian sigma=0.1; RK4 100 steps on [0,1]; Algorithm 1 from p0=0, eps=1e-6 (max-norm), maxit=200; "
             "default gain h = 1/max_i sum_j G_ij")
@@ -343,10 +343,10 @@ def run_gb300(args):
         "fp64_shoots_per_s": 1e3 / fp64_ms,
         "roofline": {"bound": "alu", "kernel": f"{kernel_name}: persistent all-pairs shoot, {4 * S} fused RK4 stages per launch",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": OWNER_LAUNCH_DRAM_BYTES if kernel_name.startswith("k_shoot_owner<1024,4>") else None,
-                     "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of one 400-stage launch of "
-                                      "k_shoot_owner<1024,4> (G=128) on this workload, from one ncu capture "
-                                      "of the current kernel (null until taken; the state is L2-resident)",
+                     "traffic": OWNER_LAUNCH_DRAM_BYTES if kernel_name == OWNER_TRAFFIC_KERNEL else None,
+                     "traffic_basis": f"dram__bytes_read.sum + dram__bytes_write.sum of one 400-stage launch of "
+                                      f"{OWNER_TRAFFIC_KERNEL} on this workload, from one ncu capture "
+                                      "(292608 + 66560 B; the state is L2-resident)",
                      "launch_us": launch_ms * 1e3, "stage_us": launch_ms * 1e3 / (4 * S),
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)",
                      "flops_per_pair": FLOPS_PER_PAIR_2D_GAUSS},
