@@ -36,6 +36,11 @@ namespace ep {
 namespace {
 
 constexpr int kChunk = 2048;  // sources staged per shared-memory fill (mixed)
+// The 2-D Gaussian stream-K kernel folds its FP32 lane sums into the FP64 accumulator
+// every kFoldChunks staged chunks (and at a segment's end): a warp's FP32 block of a
+// particle's sum is at most kFoldChunks * 2048 / 32 = 256 sources (the generic kernels
+// fold every 256 W / kChunk chunks, the same bound).
+constexpr int kFoldChunks = 4;
 // The barrier word array of the persistent shoots: [0, 8) arrival counters, [8] the
 // error flag, [kBarProgress, + kMaxPersistentCtas) one progress word per CTA.
 constexpr int kBarProgress = 16;
@@ -53,6 +58,8 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
 {
     constexpr int W = THREADS / 32;
     constexpr int V = DIM == 2 ? 1 : 2;  // float4 per particle
+    // chunks per FP32 block: a warp's block of a particle's sum stays <= 256 sources
+    constexpr int FOLD = (256 * W) / kChunk > 0 ? (256 * W) / kChunk : 1;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = a.n;
@@ -83,17 +90,18 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                 for (int c = 0; c < DIM; ++c) { qi[r][c] = 0.0f; pi[r][c] = 0.0f; }
             }
         }
+        // the lane's two particles' sums, FP32 over FOLD staged chunks, then folded
+        float acc[2][kKWidth];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int t = 0; t < kKWidth; ++t) acc[r][t] = 0.0f;
+        int nchunk = 0;
         for (int cj = j0; cj < j1; cj += kChunk) {
             const int L = min(kChunk, j1 - cj);
             __syncthreads();
             for (int t = threadIdx.x; t < L * V; t += THREADS) smem[t] = __ldcg(a.S_in + (size_t)cj * V + t);
             __syncthreads();
-            // the lane's two particles' sums over this chunk's warp share, FP32
-            float acc[2][kKWidth];
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int t = 0; t < kKWidth; ++t) acc[r][t] = 0.0f;
             const int ja = warp * L / W, jb = (warp + 1) * L / W;
 #pragma unroll 4
             for (int j = ja; j < jb; ++j) {
@@ -132,14 +140,18 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                     }
                 }
             }
-            // warps' partials -> shared memory [W][6][64] -> double-FP32 over the warps ->
+            if (++nchunk % FOLD != 0 && cj + kChunk < j1) continue;
+            // fold: warps' partials -> shared memory [W][6][64] -> double-FP32 over the warps ->
             // the FP64 accumulator (exact conversion)
             __syncthreads();
             float* red = reinterpret_cast<float*>(smem);
 #pragma unroll
             for (int r = 0; r < 2; ++r)
 #pragma unroll
-                for (int t = 0; t < kKWidth; ++t) red[(warp * kKWidth + t) * kTileI + lane + 32 * r] = acc[r][t];
+                for (int t = 0; t < kKWidth; ++t) {
+                    red[(warp * kKWidth + t) * kTileI + lane + 32 * r] = acc[r][t];
+                    acc[r][t] = 0.0f;
+                }
             __syncthreads();
             for (int t = threadIdx.x; t < kKWidth * kTileI; t += THREADS) {
                 const int k = t / kTileI, il = t % kTileI;
@@ -549,6 +561,13 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
             mq = fmaxf(mq, fmaf(qx[r], qx[r], qy[r] * qy[r]));
         }
         const bool factored = !__syncthreads_or(mq > kFactorMax);
+        // per particle: (sum g px, sum g py), (sum g x px, sum g x py), (sum g y px, sum g y py),
+        // packed so every accumulation is one f32x2 FMA; FP32 over kFoldChunks staged chunks
+        // (a warp's block: at most kFoldChunks * kChunkG / W = 256 sources), then folded
+        float2 sqv[RI], sbx[RI], sby[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
+        int nchunk = 0;
         for (int cj = j0; cj < j1; cj += kChunkG) {
             const int L = min(kChunkG, j1 - cj);
             __syncthreads();
@@ -560,11 +579,6 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
                 recB[t] = y * v.w;
             }
             __syncthreads();
-            // per particle: (sum g px, sum g py), (sum g x px, sum g x py), (sum g y px, sum g y py),
-            // packed so every accumulation is one f32x2 FMA; FP32 over this chunk's warp share
-            float2 sqv[RI], sbx[RI], sby[RI];
-#pragma unroll
-            for (int r = 0; r < RI; ++r) sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
             const int ja = warp * L / W, jb = (warp + 1) * L / W;
             if (factored) {
 #pragma unroll 2
@@ -601,7 +615,8 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
                     }
                 }
             }
-            // per particle: dq = E sq, M = q'' (x) dq - E sb  (E = 1 in the difference form)
+            if (++nchunk % kFoldChunks != 0 && cj + kChunkG < j1) continue;
+            // fold: per particle dq = E sq, M = q'' (x) dq - E sb  (E = 1 in the difference form)
             __syncthreads();
             float* red = reinterpret_cast<float*>(smem);  // [W][6][kTileG]
 #pragma unroll
@@ -615,6 +630,7 @@ __device__ __forceinline__ void stage_pairs_gauss2(const StageArgs& a, float4* s
                 o[3 * kTileG] = fmaf(qx[r], d1, -E * sbx[r].y);
                 o[4 * kTileG] = fmaf(qy[r], d0, -E * sby[r].x);
                 o[5 * kTileG] = fmaf(qy[r], d1, -E * sby[r].y);
+                sqv[r] = sbx[r] = sby[r] = make_float2(0.0f, 0.0f);
             }
             __syncthreads();
             // the warps' blocks in double-FP32, added to K in FP64 (exact conversion)
