@@ -58,6 +58,9 @@ FP64_LANES_PER_SM = 2  # FP64 FMA per clock per SM (one warp instruction per 64 
 # N = 4096 workload, from one ncu capture of that launch; reset to None when the kernel changes
 OWNER_LAUNCH_DRAM_BYTES = 292608 + 66560
 OWNER_TRAFFIC_KERNEL = "k_shoot_owner<512,8> (G=128)"
+# L2 bytes (lts__t_bytes.sum) of one cell-list stage on the 512 x 512 jittered grid: scan
+# 1.47 MB + scatter 28.0 MB + sweep 89.8 MB, from one ncu capture of a 1-step shoot
+CELL_STAGE_L2_BYTES = 1466720 + 28011072 + 89718496
 WORKLOAD = ("fourier_curve_warp: N=4096 2-D landmarks on a random Fourier curve -> sine warp; "
             "Gaussian sigma=0.1; RK4 100 steps on [0,1]; Algorithm 1 from p0=0, eps=1e-6 (max-norm), maxit=200; "
             "default gain h = 1/max_i sum_j G_ij")
@@ -381,6 +384,25 @@ def _events_ms(torch, stream, fn, reps):
     return a.elapsed_time(b) / reps, r
 
 
+def _l2_copy_gbs(torch) -> float:
+    """Copy bandwidth of a 32 MiB -> 32 MiB copy that stays in the 129 MB L2 (read + write
+    bytes per second, best of 5 x 50 copies): the L2 roofline's denominator."""
+    a = torch.ones(8 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for _ in range(5):
+        e0.record()
+        for _ in range(50):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 50 * 2 * a.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
 def _alu_roofline(flops_per_s: float, peak_tflops: float, note: str) -> dict:
     a = flops_per_s / 1e12
     return {"bound": "alu", "achieved": a, "peak": peak_tflops, "unit": "TFLOP/s", "frac": a / peak_tflops,
@@ -406,6 +428,7 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True, ba
     import torch
 
     out = {}
+    l2_gbs = _l2_copy_gbs(torch)
     hbm = None
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -426,6 +449,14 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True, ba
                         "roofline": {"bound": "hbm", "achieved": byts / (stage_us * 1e-6) / 1e9, "peak": hbm,
                                      "unit": "GB/s", "frac": byts / (stage_us * 1e-6) / 1e9 / hbm,
                                      "bytes_per_stage": byts, "note": "working set is L2-resident"},
+                        "roofline_l2": {"bound": "l2", "achieved": byts / (stage_us * 1e-6) / 1e9, "peak": l2_gbs,
+                                        "unit": "GB/s", "frac": byts / (stage_us * 1e-6) / 1e9 / l2_gbs,
+                                        "traffic": CELL_STAGE_L2_BYTES,
+                                        "traffic_frac": CELL_STAGE_L2_BYTES / (stage_us * 1e-6) / 1e9 / l2_gbs,
+                                        "peak_basis": "L2-resident 32 MiB -> 32 MiB copy measured in this run "
+                                                      "(read + write bytes, best of 5 x 50 copies)",
+                                        "traffic_basis": "lts__t_bytes.sum of one stage's scan, scatter and sweep "
+                                                         "(ncu, profiles/k_cell_sweep_jittered_grid_512.md)"},
                         "roofline_alu": _alu_roofline(acc_pairs * FLOPS_PER_PAIR_2D_TENT / (stage_us * 1e-6), peak_tflops,
                                                       f"{FLOPS_PER_PAIR_2D_TENT} flop per accepted pair")}
     if with_cpu:
