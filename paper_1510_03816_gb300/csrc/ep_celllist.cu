@@ -45,6 +45,12 @@ constexpr int kSweepRI = 1;                    // particles of one cell per swee
 constexpr int kSweepCap = 2048;                // halo records staged in shared memory (~2x the mean halo)
 constexpr int kScanBlock = 4096;               // cells per scan block (1024 threads x 4)
 constexpr int kMaxCellsPerAxis2D = 2048;
+// Slot layout: cell k's records at slots [k kSlotCap, k kSlotCap + count[k]), written by
+// the binning itself, so a stage needs no scan and no scatter.  Used while the grid's
+// slots fit kSlotFactor n and no cell holds more than kSlotCap particles; a cell that
+// overflows raises a flag and the next stage takes the scanned layout instead.
+constexpr int kSlotCap = 32;
+constexpr int kSlotFactor = 8;
 
 struct Grid {
     double lo[2], h[2], inv_h[2];
@@ -67,12 +73,17 @@ struct Impl {
     int* rank;
     int* sidx;       // particle index of each sorted slot
     float4* srec;    // records in cell order
-    int* count[2];   // per cell (ping-pong by stage), then local exclusive scan
+    int* count[3];   // per cell (rotating by stage: read, binned into, zeroed), then local exclusive scan
+    float4* frec[2]; // slot layout of the records (by stage parity)
+    int* fidx[2];    // slot layout of the particle indices
+    int* ovf;        // [3] per count buffer: a cell's count exceeded kSlotCap
     int* bsum;       // per scan block total, then exclusive block offsets
     int* scan_ctr;   // arrival counter of the block scan
     double* bbox;    // keys (k_bbox2) of min x, min y, max x, max y
     Grid g;
     int cur;         // count buffer holding the next stage's bins
+    int par;         // slot layout the next stage reads
+    int slots;       // the grid's slots fit (kSlotCap ncell <= kSlotFactor n)
 };
 
 static_assert(sizeof(Impl) <= 1024, "Impl must fit the CellBufs host block");
@@ -86,9 +97,18 @@ struct Args {
     double dp_scale;
     double sigma;
     Grid g;
-    const int* count;   // local scan
+    const int* count;   // local scan (scanned layout) or cell counts (slot layout)
     const int* boff;    // block offsets
-    int* count_next;    // bins of the next stage (zeroed by this stage's scan)
+    int* count_next;    // bins of the next stage
+    int* count_zero;    // the count buffer of the stage after next, zeroed here
+    int slots;          // slot layout available for this grid
+    const int* ovf_in;  // a cell of this stage's bins overflowed: scanned layout
+    int* ovf_out;       // raised when a next-stage bin overflows
+    int* ovf_zero;      // the flag of the stage after next, cleared here
+    const float4* frec_in;
+    const int* fidx_in;
+    float4* frec_out;
+    int* fidx_out;
     int* key_out;
     int* rank_out;
     const int* sidx;
@@ -184,7 +204,8 @@ __global__ void __launch_bounds__(256) k_bbox2(const double* __restrict__ q, int
 // x = (q, p) and the step-start cells / records from FP64.
 __global__ void k_cell_anchor(const double* __restrict__ q, const double* __restrict__ p, int n, Grid g,
                               double* __restrict__ x, int2* __restrict__ cellX, float4* __restrict__ recX,
-                              int* __restrict__ count, int* __restrict__ key, int* __restrict__ rank)
+                              int* __restrict__ count, int* __restrict__ key, int* __restrict__ rank, int slots,
+                              float4* __restrict__ frec, int* __restrict__ fidx, int* __restrict__ ovf)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -201,10 +222,20 @@ __global__ void k_cell_anchor(const double* __restrict__ q, const double* __rest
     locate(qx, 0, g, cx, ox);
     locate(qy, 1, g, cy, oy);
     cellX[i] = make_int2(cx, cy);
-    recX[i] = make_float4(ox, oy, (float)px, (float)py);
+    const float4 r = make_float4(ox, oy, (float)px, (float)py);
+    recX[i] = r;
     const int k = cy * g.nc[0] + cx;
     key[i] = k;
-    rank[i] = atomicAdd(count + k, 1);
+    const int rk = atomicAdd(count + k, 1);
+    rank[i] = rk;
+    if (slots) {
+        if (rk < kSlotCap) {
+            frec[(size_t)k * kSlotCap + rk] = r;
+            fidx[(size_t)k * kSlotCap + rk] = i;
+        } else {
+            *ovf = 1;
+        }
+    }
 }
 
 // Exclusive scan of 4 x 1024 values in place (one CTA); returns nothing.
@@ -244,18 +275,16 @@ __device__ void cta_exclusive_scan4(int* __restrict__ v, long long count, int* s
 
 // Exclusive scan of the cell counts within blocks of kScanBlock cells; bsum[b] =
 // block total.  The last block to finish scans the block totals into block
-// offsets.  Also zeroes the other count buffer (the next stage's bins).
+// offsets.  Only for the scanned layout: with the slot layout in use (slots and no
+// overflow flag) the kernel returns at once.
 __global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, long long ncell, int* __restrict__ bsum,
-                                                     int* __restrict__ zero_next, int* __restrict__ ctr, int nb)
+                                                     int* __restrict__ ctr, int nb, int slots, const int* __restrict__ ovf)
 {
     __shared__ int sw[32];
     __shared__ int last;
+    if (slots && *ovf == 0) return;
     int* blk = count + (long long)blockIdx.x * kScanBlock;
     const long long cnt = min((long long)kScanBlock, ncell - (long long)blockIdx.x * kScanBlock);
-    for (int k = 0; k < 4; ++k) {
-        const long long c = (long long)blockIdx.x * kScanBlock + 4LL * threadIdx.x + k;
-        if (c < ncell) zero_next[c] = 0;
-    }
     // block total first (the scan overwrites the counts)
     int s = 0;
     for (int k = 0; k < 4; ++k) {
@@ -285,14 +314,15 @@ __global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, lo
 
 __global__ void k_cell_scatter(const int* __restrict__ key, const int* __restrict__ rank, const int* __restrict__ count,
                                const int* __restrict__ boff, const float4* __restrict__ recIn, int n,
-                               int* __restrict__ sidx, float4* __restrict__ srec)
+                               int* __restrict__ sidx, float4* __restrict__ srec, int slots, const int* __restrict__ ovf)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int k = key[i];
-    const int slot = cell_start(count, boff, k) + rank[i];
-    sidx[slot] = i;
-    srec[slot] = recIn[i];
+    if (slots && *ovf == 0) return;  // the slot layout is in use
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k = key[i];
+        const int slot = cell_start(count, boff, k) + rank[i];
+        sidx[slot] = i;
+        srec[slot] = recIn[i];
+    }
 }
 
 // Finish particle i: RHS output, or the RK4 stage plus the binning of the
@@ -347,7 +377,16 @@ __device__ void epilogue(const Args& a, int i, float dqx, float dqy, float dpx, 
     }
     const int k = c1 * a.g.nc[0] + c0;
     a.key_out[i] = k;
-    a.rank_out[i] = atomicAdd(a.count_next + k, 1);
+    const int rk = atomicAdd(a.count_next + k, 1);
+    a.rank_out[i] = rk;
+    if (a.slots) {
+        if (rk < kSlotCap) {
+            a.frec_out[(size_t)k * kSlotCap + rk] = a.recOut[i];
+            a.fidx_out[(size_t)k * kSlotCap + rk] = i;
+        } else {
+            *a.ovf_out = 1;
+        }
+    }
 }
 
 // Exclusive prefix sum of NV values (NV <= 4 x 32) by one warp: out[t] for t < NV,
@@ -414,19 +453,36 @@ __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
     const int warp = threadIdx.x >> 5;
     const int ncx = a.g.nc[0], ncy = a.g.nc[1];
     const int cx0 = blockIdx.x * kBlk, cy0 = blockIdx.y * kBlk;
+    // this stage's layout: slots (each cell at k kSlotCap, count[k] long) or scanned
+    const bool use_slots = a.slots && *a.ovf_in == 0;
     for (int t = threadIdx.x; t < NH; t += kSweepThreads) {
         const int hx = t % kHalo, hy = t / kHalo;
         const int row = cy0 - 1 + hy, col = cx0 - 1 + hx;
         int gs = 0, len = 0;
         if (row >= 0 && row < ncy && col >= 0 && col < ncx) {
             const long long c = (long long)row * ncx + col;
-            gs = cell_start(a.count, a.boff, c);
-            const int ge = (c + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c + 1) : a.n;
-            len = ge - gs;
+            if (use_slots) {
+                gs = (int)(c * kSlotCap);
+                len = a.count[c];
+            } else {
+                gs = cell_start(a.count, a.boff, c);
+                const int ge = (c + 1 < a.g.ncell) ? cell_start(a.count, a.boff, c + 1) : a.n;
+                len = ge - gs;
+            }
         }
         c_gs[t] = gs;
         c_len[t] = len;
     }
+    // the bins of the stage after next start from zero: this CTA's own cells
+    if (a.count_zero) {
+        for (int t = threadIdx.x; t < kBlk * kBlk; t += kSweepThreads) {
+            const int row = cy0 + t / kBlk, col = cx0 + t % kBlk;
+            if (row < ncy && col < ncx) a.count_zero[(long long)row * ncx + col] = 0;
+        }
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *a.ovf_zero = 0;
+    }
+    const int* gidx = use_slots ? a.fidx_in : a.sidx;
+    const float4* grec = use_slots ? a.frec_in : a.srec;
     __syncthreads();
     if (warp == 0) warp_exclusive_scan<NH>([&](int t) { return c_len[t]; }, c_start);
     if (warp == 1)
@@ -440,16 +496,16 @@ __global__ void __launch_bounds__(kSweepThreads) k_cell_sweep(Args a)
             const int t = find_segment(c_start, NH, u);
             const int g0 = c_gs[t], len = c_len[t];
             const int g = g0 + (u - c_start[t]);
-            const int my = __ldg(a.sidx + g);
+            const int my = __ldg(gidx + g);
             int rank = 0;
-            for (int v = 0; v < len; ++v) rank += __ldg(a.sidx + g0 + v) < my ? 1 : 0;
+            for (int v = 0; v < len; ++v) rank += __ldg(gidx + g0 + v) < my ? 1 : 0;
             s_idx[c_start[t] + rank] = my;
-            s_rec[c_start[t] + rank] = __ldg(a.srec + g);
+            s_rec[c_start[t] + rank] = __ldg(grec + g);
         }
         __syncthreads();
     }
-    const float4* rec = sm ? s_rec : a.srec;
-    const int* idx = sm ? s_idx : a.sidx;
+    const float4* rec = sm ? s_rec : grec;
+    const int* idx = sm ? s_idx : gidx;
     const int* cst = sm ? c_start : c_gs;
     const float e0 = a.g.e[0], e1 = a.g.e[1];
     const int ntask = t_pre[NO];
@@ -560,11 +616,15 @@ size_t impl_bytes(int n)
     z.add(sizeof(int) * (size_t)n * 3);
     z.add(sizeof(float4) * (size_t)n);
     const size_t maxcell = (size_t)kMaxCellsPerAxis2D * kMaxCellsPerAxis2D;
-    z.add(sizeof(int) * maxcell);
-    z.add(sizeof(int) * maxcell);
+    for (int k = 0; k < 3; ++k) z.add(sizeof(int) * maxcell);
     z.add(sizeof(int) * (maxcell / kScanBlock + 1));
     z.add(sizeof(int) * 4);
     z.add(sizeof(double) * 4);
+    for (int k = 0; k < 2; ++k) {
+        z.add(sizeof(float4) * (size_t)kSlotFactor * n);
+        z.add(sizeof(int) * (size_t)kSlotFactor * n);
+    }
+    z.add(sizeof(int) * 4);
     return z.total;
 }
 
@@ -575,18 +635,33 @@ ep_status run_stage(const ep_params& P, const CellBufs& b, Args a, const float4*
     Impl* im = impl_of(b);
     const Grid& g = im->g;
     const int n = b.n;
-    const unsigned gn = (unsigned)((n + 255) / 256);
+    // the scatter strides over the particles with a small grid (so that, with the slot
+    // layout in use, its early return costs little)
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    const unsigned gn = (unsigned)std::max(1, std::min((n + 255) / 256, 2 * di.sm_count));
     const int nb = (int)((g.ncell + kScanBlock - 1) / kScanBlock);
-    int* cnt = im->count[im->cur];
-    int* nxt = im->count[im->cur ^ 1];
+    const int cur = im->cur, nx = (cur + 1) % 3, nn = (cur + 2) % 3;
+    int* cnt = im->count[cur];
     count_launch(2);
-    k_scan_local<<<nb, 1024, 0, st>>>(cnt, g.ncell, im->bsum, nxt, im->scan_ctr, nb);
-    k_cell_scatter<<<gn, 256, 0, st>>>(im->key, im->rank, cnt, im->bsum, recIn, n, im->sidx, im->srec);
+    // scan and scatter run only for the scanned layout (they return at once otherwise)
+    k_scan_local<<<nb, 1024, 0, st>>>(cnt, g.ncell, im->bsum, im->scan_ctr, nb, im->slots, im->ovf + cur);
+    k_cell_scatter<<<gn, 256, 0, st>>>(im->key, im->rank, cnt, im->bsum, recIn, n, im->sidx, im->srec, im->slots,
+                                       im->ovf + cur);
     a.n = n;
     a.g = g;
     a.count = cnt;
     a.boff = im->bsum;
-    a.count_next = nxt;
+    a.count_next = im->count[nx];
+    a.count_zero = a.mode == 0 ? im->count[nn] : nullptr;
+    a.slots = im->slots;
+    a.ovf_in = im->ovf + cur;
+    a.ovf_out = im->ovf + nx;
+    a.ovf_zero = im->ovf + nn;
+    a.frec_in = im->frec[im->par];
+    a.fidx_in = im->fidx[im->par];
+    a.frec_out = im->frec[im->par ^ 1];
+    a.fidx_out = im->fidx[im->par ^ 1];
     a.key_out = im->key;
     a.rank_out = im->rank;
     a.sidx = im->sidx;
@@ -607,7 +682,10 @@ ep_status run_stage(const ep_params& P, const CellBufs& b, Args a, const float4*
     else
         k_cell_sweep<0, kSweepRI><<<grid, kSweepThreads, 0, st>>>(a);
     EP_TRY_CUDA(cudaGetLastError());
-    if (a.mode == 0) im->cur ^= 1;
+    if (a.mode == 0) {
+        im->cur = nx;
+        im->par ^= 1;
+    }
     return EP_OK;
 }
 
@@ -640,11 +718,16 @@ ep_status load_anchor(const ep_params& P, CellBufs& b, const double* q, const do
     for (int k = 0; k < 4; ++k) bb[k] = dkey_value(kb[k]);
     im->g = make_grid(bb, P.sigma);
     im->cur = 0;
+    im->par = 0;
+    im->slots = im->g.ncell * kSlotCap <= (long long)kSlotFactor * n ? 1 : 0;
     EP_TRY_CUDA(cudaMemsetAsync(im->count[0], 0, sizeof(int) * (size_t)im->g.ncell, st));
+    EP_TRY_CUDA(cudaMemsetAsync(im->count[1], 0, sizeof(int) * (size_t)im->g.ncell, st));
     EP_TRY_CUDA(cudaMemsetAsync(im->scan_ctr, 0, sizeof(int) * 4, st));
+    EP_TRY_CUDA(cudaMemsetAsync(im->ovf, 0, sizeof(int) * 4, st));
     count_launch();
     k_cell_anchor<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, p, n, im->g, write_x ? b.x : nullptr, im->cellX,
-                                                                im->recX, im->count[0], im->key, im->rank);
+                                                                im->recX, im->count[0], im->key, im->rank, im->slots,
+                                                                im->frec[0], im->fidx[0], im->ovf);
     EP_TRY_CUDA(cudaGetLastError());
     return EP_OK;
 }
@@ -680,12 +763,16 @@ ep_status cell_carve(Arena* ar, int n, int dim, int prec, CellBufs* b)
     im->sidx = (int*)ar->carve(sizeof(int) * (size_t)n);
     im->srec = (float4*)ar->carve(sizeof(float4) * (size_t)n);
     const size_t maxcell = (size_t)kMaxCellsPerAxis2D * kMaxCellsPerAxis2D;
-    im->count[0] = (int*)ar->carve(sizeof(int) * maxcell);
-    im->count[1] = (int*)ar->carve(sizeof(int) * maxcell);
+    for (int k = 0; k < 3; ++k) im->count[k] = (int*)ar->carve(sizeof(int) * maxcell);
     im->bsum = (int*)ar->carve(sizeof(int) * (maxcell / kScanBlock + 1));
     im->scan_ctr = (int*)ar->carve(sizeof(int) * 4);
     im->bbox = (double*)ar->carve(sizeof(double) * 4);
-    if (!im->bbox) return set_error("workspace too small for the cell list"), EP_ENOMEM;
+    for (int k = 0; k < 2; ++k) {
+        im->frec[k] = (float4*)ar->carve(sizeof(float4) * (size_t)kSlotFactor * n);
+        im->fidx[k] = (int*)ar->carve(sizeof(int) * (size_t)kSlotFactor * n);
+    }
+    im->ovf = (int*)ar->carve(sizeof(int) * 4);
+    if (!im->ovf) return set_error("workspace too small for the cell list"), EP_ENOMEM;
     return EP_OK;
 }
 
