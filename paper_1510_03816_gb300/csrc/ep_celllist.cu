@@ -27,6 +27,7 @@
 // anchor + c dt k in FP32 on the offsets (re-celled by floor(o / e)); the step
 // state x is FP64 and the anchor is re-derived from it in FP64 every step.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -719,7 +720,9 @@ ep_status load_anchor(const ep_params& P, CellBufs& b, const double* q, const do
     im->g = make_grid(bb, P.sigma);
     im->cur = 0;
     im->par = 0;
-    im->slots = im->g.ncell * kSlotCap <= (long long)kSlotFactor * n ? 1 : 0;
+    // EP_CELL_SLOTS=0 in the environment keeps the scanned layout (same sums, bit for bit)
+    const char* es = getenv("EP_CELL_SLOTS");
+    im->slots = (im->g.ncell * kSlotCap <= (long long)kSlotFactor * n && !(es && es[0] == '0')) ? 1 : 0;
     EP_TRY_CUDA(cudaMemsetAsync(im->count[0], 0, sizeof(int) * (size_t)im->g.ncell, st));
     EP_TRY_CUDA(cudaMemsetAsync(im->count[1], 0, sizeof(int) * (size_t)im->g.ncell, st));
     EP_TRY_CUDA(cudaMemsetAsync(im->scan_ctr, 0, sizeof(int) * 4, st));

@@ -155,3 +155,50 @@ def test_dense_cluster_beyond_the_staging_capacity():
     q1, p1 = ep.shoot(cuda(X), cuda(p), prm)
     rq, rp = o.shoot(X, p, ep.TENT, sigma, 4)
     assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
+
+
+def _converging_ring():
+    """A 40 x 40 jittered grid (tent sigma = 0.05, about 11 particles per cell, so the
+    cell grid's slots fit) with a ring of 60 particles moving in on its centre: the ring
+    piles more than 32 particles into one cell after the first step and spreads out again
+    later, so a shoot switches from the slot layout to the scanned one and back."""
+    sig = 0.05
+    g = np.linspace(0.2, 0.8, 40)
+    rng = np.random.default_rng(7)
+    B = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2) + rng.uniform(-0.003, 0.003, (1600, 2))
+    th = np.linspace(0, 2 * np.pi, 60, endpoint=False)
+    ring = 0.5 + 0.12 * np.stack([np.cos(th), np.sin(th)], 1)
+    X = np.vstack([B, ring])
+    p = np.zeros_like(X)
+    p[1600:] = -(ring - 0.5)
+    return X, p, sig
+
+
+def test_slot_and_scanned_layouts_agree_through_overflow():
+    import os
+
+    X, p, sig = _converging_ring()
+    # the oracle's trajectory: some cell of the sweep grid (edge sigma (1 + 2^-8), origin
+    # min - 2 h) holds more than 32 particles mid-shoot but not at the first step
+    h = sig * 1.00390625
+    lo = X.min(0) - 2 * h
+    q, pp, most = X.copy(), p.copy(), []
+    for _ in range(20):
+        q, pp = o.shoot(q, pp, ep.TENT, sig, 1, 0.05)
+        c = np.floor((q - lo) / h).astype(int)
+        most.append(np.unique(c[:, 1] * 4096 + c[:, 0], return_counts=True)[1].max())
+    assert most[0] <= 32 and max(most) > 40
+    prm = ep.params(dim=2, kernel=ep.TENT, sigma=sig, steps=20, precision=ep.MIXED, neigh=ep.CELLLIST)
+    q1, p1 = ep.shoot(cuda(X), cuda(p), prm)
+    old = os.environ.get("EP_CELL_SLOTS")
+    try:
+        os.environ["EP_CELL_SLOTS"] = "0"
+        q2, p2 = ep.shoot(cuda(X), cuda(p), prm)
+    finally:
+        if old is None:
+            os.environ.pop("EP_CELL_SLOTS", None)
+        else:
+            os.environ["EP_CELL_SLOTS"] = old
+    assert torch.equal(q1, q2) and torch.equal(p1, p2)  # both layouts sum cells in particle-index order
+    rq, rp = o.shoot(X, p, ep.TENT, sig, 20)
+    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
