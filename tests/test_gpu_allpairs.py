@@ -207,3 +207,24 @@ def test_empty_and_invalid_inputs():
         ep.shoot(cuda(np.zeros((4, 2))), cuda(np.zeros((4, 2))), ep.params(dim=2, steps=0))
     with pytest.raises(ep.EPError):
         ep.rhs(cuda(np.zeros((4, 2))), cuda(np.zeros((4, 2))), ep.params(dim=2, kernel=ep.GAUSS, neigh=ep.CELLLIST))
+
+
+@pytest.mark.parametrize("n", [3700, 4096, 1000, 301])
+def test_owner_kernel_default_forms_parity(n, monkeypatch):
+    """The persistent 2-D Gaussian shoot in its default configuration (EP_AUTOTUNE=0):
+    the 512-thread form with 8 rows per lane for n >= 24 rows per SM (3700: ragged rows
+    per CTA), the 1024-thread form with 8-row sub-tiles below; endpoints against the
+    oracle within 1e-4, and the form the launch used is the owner kernel."""
+    monkeypatch.setenv("EP_AUTOTUNE", "0")
+    pr = w.fourier_curve_warp(n=n)
+    p0 = 0.004 * (pr.Y - pr.X)
+    prm = ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=6, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    ep.set_launch_timing(True)
+    try:
+        q1, p1 = ep.shoot(cuda(pr.X), cuda(p0), prm)
+        _, kname = ep.last_launch()
+    finally:
+        ep.set_launch_timing(False)
+    assert kname.startswith("k_shoot_owner<512,8>" if n >= 3648 else "k_shoot_owner<1024,16>"), kname
+    rq, rp = o.shoot(pr.X, p0, pr.kernel, pr.sigma, 6)
+    assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
