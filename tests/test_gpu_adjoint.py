@@ -2,9 +2,11 @@
 (ep_adjoint) against the FP64 CPU oracle, through the C ABI.
 
 Tolerances: FP64 mode <= 1e-10 (relative max-norm); mixed precision (FP32 pair
-terms, FP64 sums): HVP <= 1e-4, gradient <= 1e-3, energy <= 1e-5.  The mixed
-gradient at the full 3-D size is checked by a directional finite difference of
-the energy, a property that holds at any size.
+terms, FP64 sums): HVP <= 1e-5 (the RHS bound; measured <= 1.4e-6), gradient
+<= 1e-4 (the shot-endpoint bound; measured <= 2e-7, and 9.5e-7 against the FP64
+gradient at N = 16384 3-D), energy <= 1e-5.  The mixed gradient at the full 3-D
+size is also checked by a directional finite difference of the energy, a property
+that holds at any size.
 """
 import numpy as np
 import pytest
@@ -65,7 +67,7 @@ def test_hvp_parity(prec, kernel, sigma, dim):
     prm = ep.params(dim=dim, kernel=kernel, sigma=sigma, precision=prec, neigh=ep.ALLPAIRS)
     hq, hp = ep.hvp(cuda(q), cuda(p), cuda(vq), cuda(vp), prm)
     rq, rp = o.hvp(q, p, vq, vp, kernel, sigma)
-    tol = 1e-10 if prec == ep.FP64 else 1e-4
+    tol = 1e-10 if prec == ep.FP64 else 1e-5
     assert rel(hq, rq) < tol
     assert rel(hp, rp) < tol
 
@@ -87,7 +89,7 @@ def test_adjoint_parity(prec, kernel, sigma, dim):
     if prec == ep.FP64:
         assert rel(g, gr) < 1e-10 and abs(E - Er) < 1e-10 * abs(Er)
     else:
-        assert rel(g, gr) < 1e-3 and abs(E - Er) < 1e-5 * abs(Er)
+        assert rel(g, gr) < 1e-4 and abs(E - Er) < 1e-5 * abs(Er)
 
 
 def test_adjoint_checkpoint_interval_does_not_change_the_result():
@@ -159,5 +161,5 @@ def test_adjoint_full_size_star_surface_fp64_central_differences():
     assert abs(fd - dd) < 1e-6 * abs(dd)
     prm_m = ep.params(dim=3, kernel=pr.kernel, sigma=pr.sigma, steps=pr.steps, precision=ep.MIXED)
     Em, gm = ep.adjoint(X, p0, Y, prm_m, pr.lam, ckpt_every=10)
-    assert rel(gm, g.cpu().numpy()) < 1e-3
+    assert rel(gm, g.cpu().numpy()) < 1e-4
     assert abs(Em - E) < 1e-4 * abs(E)

@@ -68,7 +68,7 @@ def test_shoot_parity(prec, kernel, sigma, dim):
     prm = ep.params(dim=dim, kernel=kernel, sigma=sigma, steps=6, precision=prec, neigh=ep.ALLPAIRS, inexact=S2)
     q1, p1 = ep.shoot(cuda(q), cuda(p), prm)
     rq, rp = o.shoot_inexact(q, p, kernel, sigma, S2, 6)
-    tol = 1e-12 if prec == ep.FP64 else (1e-3 if kernel == ep.TENT else 1e-4)
+    tol = 1e-12 if prec == ep.FP64 else 1e-4
     assert rel(q1, rq) < tol and rel(p1, rp) < tol
 
 
@@ -98,7 +98,7 @@ def test_match_momentum_difference_stop(prec):
         1e-12 if prec == ep.FP64 else 1e-6) * r.h
     assert rel(r.p0, p) < tol
     assert len(r.hist) == len(hist) == it
-    np.testing.assert_allclose(r.hist, hist, rtol=tol if prec == ep.FP64 else 1e-3)
+    np.testing.assert_allclose(r.hist, hist, rtol=tol)
 
 
 def test_paths_without_the_inexact_system_refuse_it():
