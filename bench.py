@@ -56,7 +56,7 @@ FLOPS_PER_PAIR_2D_TANGENT = 58  # FP64 tangent pair: d, dd (4), r^2, d.dd, p.p (
 FP64_LANES_PER_SM = 2  # FP64 FMA per clock per SM (one warp instruction per 64 cycles per SMSP)
 # DRAM bytes (read + write) of one 400-stage launch of k_shoot_owner<512,8> (G=128) on the
 # N = 4096 workload, from one ncu capture of that launch; reset to None when the kernel changes
-OWNER_LAUNCH_DRAM_BYTES = 292608 + 66560
+OWNER_LAUNCH_DRAM_BYTES = 292352 + 49920
 OWNER_TRAFFIC_KERNEL = "k_shoot_owner<512,8> (G=128)"
 # L2 bytes (lts__t_bytes.sum) of one cell-list stage on the 512 x 512 jittered grid: scan
 # 1.47 MB + scatter 28.0 MB + sweep 89.8 MB, from one ncu capture of a 1-step shoot
@@ -334,7 +334,8 @@ def run_gb300(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "rk4_steps": S, "precision": "FP32 pair terms; per-particle sums FP32 within 128-source warp blocks, accumulated across blocks in double-FP32 (TwoSum, FP64-level); FP64 step state, residual and update",
+        "config": {"workload": WORKLOAD, "n": n, "rk4_steps": S, "precision": "FP32 pair terms; per-particle sums FP32 within warp blocks of at most 256 sources, accumulated across blocks in double-FP32 (TwoSum, FP64-level); FP64 step state, residual and update",
+                   "loop": "Algorithm 1 as one CUDA graph per matching: a while-loop node over the persistent shoot and a one-CTA kernel for the FP64 residual, stop tests, update and next load (no host round trip per update)",
                    "shoots_per_step": shoots / args.steps, "l2": "256 MiB buffer written between steps (untimed)",
                    "parallelism": f"replicas x{world}"},
         "final": {"status": ep.STATUS_NAMES.get(last.status, last.status), "iters": last.iters,
@@ -349,7 +350,7 @@ def run_gb300(args):
                      "traffic": OWNER_LAUNCH_DRAM_BYTES if kernel_name == OWNER_TRAFFIC_KERNEL else None,
                      "traffic_basis": f"dram__bytes_read.sum + dram__bytes_write.sum of one 400-stage launch of "
                                       f"{OWNER_TRAFFIC_KERNEL} on this workload, from one ncu capture "
-                                      "(292608 + 66560 B; the state is L2-resident)",
+                                      "(292352 + 49920 B; the state is L2-resident)",
                      "launch_us": launch_ms * 1e3, "stage_us": launch_ms * 1e3 / (4 * S),
                      "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived, not measured)",
                      "flops_per_pair": FLOPS_PER_PAIR_2D_GAUSS},
@@ -656,7 +657,7 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True, ba
                              "seconds_per_match": dt, "matchings_per_s": 1.0 / dt, "iters": r.iters, "status": r.status,
                              "resid": r.resid, "krylov_products": r.products,
                              "roofline": {"bound": "latency", "note": f"one launch on one CTA: {r.iters + 1} mixed shoots, FP64 "
-                                          "residuals and {r.iters} FP64 updates p0 += h G(X)^-1 r (G(X)^-1 formed "
+                                          f"residuals and {r.iters} FP64 updates p0 += h G(X)^-1 r (G(X)^-1 formed "
                                           "once from its LU factors); the oracle's time is the velocity_fp64 row's"}}
     if with_cpu:
         def run_small(o):

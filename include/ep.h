@@ -148,10 +148,16 @@ ep_status ep_shoot(const ep_params* params, int64_t n, const double* q0, const d
  * Sec. 5, applied to the momenta): repeat { Q(1) = shoot(X, p0); r = Y - Q(1);
  * stop if max|r| < eps; p0 += h r } at most info->maxit updates.  p0: in = initial
  * guess (zeros for the paper's default, Note 1 item 4), out = last iterate.  The
- * residual and the update are FP64 in both precisions.  Synchronises the stream
- * (the stopping test is read on the host each iteration; small 2-D mixed-precision
- * problems, n <= 384, run the whole loop on one CTA of the batched solver).  Returns EP_OK,
- * EP_ENOTCONVERGED or EP_EDIVERGED; info is filled in all three cases. */
+ * residual and the update are FP64 in both precisions.  Synchronises the stream.
+ * Where the loop runs: FP64 on the all-pairs path, one cooperative launch; small 2-D
+ * mixed-precision problems (n <= 384), one CTA of the batched solver; the 2-D Gaussian
+ * in mixed precision with the owner-computes shoot (n <= 4096), one CUDA graph per
+ * matching (a while-loop node over the shoot and a one-CTA kernel for the residual,
+ * the stopping test and the update; EP_DEVICE_MATCH=0 in the environment selects the
+ * host loop instead, with the same results); otherwise a host loop that reads the
+ * stopping test back each iteration.  Returns EP_OK, EP_ENOTCONVERGED or EP_EDIVERGED
+ * (EP_ETIMEOUT if a grid-barrier wait of a persistent shoot gave up); info is filled
+ * in the first three cases. */
 ep_status ep_match(const ep_params* params, int64_t n, const double* X, const double* Y,
                    double* p0, ep_match_info* info, void* stream);
 

@@ -320,6 +320,7 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
     constexpr int W = THREADS / 32;
     constexpr int RI = owner_ri<JL>();
     constexpr int RG = 32 / JL;  // row groups per warp
+    static_assert(RI % 2 == 0, "the exponents are computed for pairs of rows");
     constexpr int R = RG * RI;   // rows per sub-tile
     constexpr int CH = owner_chunk<JL>();
     constexpr int NV = RI * kKWidth;  // finalized partials per lane
@@ -381,13 +382,23 @@ __device__ __forceinline__ void stage_owner_gauss2(const StageArgs& a, float4* s
                     const float byy = recB[j];
                     const float2 pxy = make_float2(B.x, B.y), xp = make_float2(B.z, B.w);
                     const float2 yp = make_float2(A.w, byy);
+                    // the exponents of two rows in one packed FMA pair (the source's
+                    // coefficients broadcast): fewer issue slots than two scalar chains,
+                    // measured 1.5 % faster per stage here (the stream-K tiles of 4 rows
+                    // per lane measured slower with it and keep the scalar form)
 #pragma unroll
-                    for (int r = 0; r < RI; ++r) {
-                        const float g = ex2_approx(fmaf(qx[r], A.x, fmaf(qy[r], A.y, A.z)));
-                        const float2 gg = make_float2(g, g);
-                        sqv[r] = __ffma2_rn(gg, pxy, sqv[r]);
-                        sbx[r] = __ffma2_rn(gg, xp, sbx[r]);
-                        sby[r] = __ffma2_rn(gg, yp, sby[r]);
+                    for (int r = 0; r < RI; r += 2) {
+                        const float2 t = __ffma2_rn(make_float2(qx[r], qx[r + 1]), make_float2(A.x, A.x),
+                                                    __ffma2_rn(make_float2(qy[r], qy[r + 1]), make_float2(A.y, A.y),
+                                                               make_float2(A.z, A.z)));
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const float g = ex2_approx(u ? t.y : t.x);
+                            const float2 gg = make_float2(g, g);
+                            sqv[r + u] = __ffma2_rn(gg, pxy, sqv[r + u]);
+                            sbx[r + u] = __ffma2_rn(gg, xp, sbx[r + u]);
+                            sby[r + u] = __ffma2_rn(gg, yp, sby[r + u]);
+                        }
                     }
                 }
             } else {
@@ -1486,6 +1497,33 @@ struct TimedLaunch {
     }
 };
 
+// The launch configuration of the persistent 2-D Gaussian shoot in mixed precision:
+// the tuner's (tuned once per size and device, by trial shoots from the loaded state,
+// which they restore) when the tuner is on, else the default one.
+ep_status gauss2_config(const ep_params& P, const AllPairsBufs& b, const StageArgs& a, double dt, cudaStream_t st,
+                        bool tc, OwnerCfg* out)
+{
+    DeviceInfo di{};
+    EP_TRY(device_info(&di));
+    OwnerCfg c = tc ? OwnerCfg{di.sm_count, 0} : owner_default(b.n, di.sm_count);
+    if (b.x_bak && autotune_enabled()) {
+        const TuneKey key{b.n, P.dim, P.kernel, di.device, tc ? 1 : 0};
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) c = it->second, have = true;
+        }
+        if (!have) {
+            EP_TRY(tune_persistent(P, b, a, dt, st, &c, tc));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key] = c;
+        }
+    }
+    *out = c;
+    return EP_OK;
+}
+
 // The persistent (one cooperative launch) shoot of mixed precision, when it
 // applies: tuned owner / stream-K / tensor-core launch for the 2-D Gaussian, the
 // generic persistent shoot otherwise.  rec: if set, every stage input is also
@@ -1500,23 +1538,8 @@ ep_status persistent_steps(const ep_params& P, const AllPairsBufs& b, StageArgs 
     a.Sx_w = b.Sx;
     if (P.dim == 2 && P.kernel == EP_GAUSS) {
         const bool tc = !rec && tc_enabled(P) && b.part;
-        DeviceInfo di{};
-        EP_TRY(device_info(&di));
-        OwnerCfg c = tc ? OwnerCfg{di.sm_count, 0} : owner_default(b.n, di.sm_count);
-        if (b.x_bak && autotune_enabled()) {
-            const TuneKey key{b.n, P.dim, P.kernel, di.device, tc ? 1 : 0};
-            bool have = false;
-            {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                auto it = g_tuned.find(key);
-                if (it != g_tuned.end()) c = it->second, have = true;
-            }
-            if (!have) {
-                EP_TRY(tune_persistent(P, b, a, dt, st, &c, tc));
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tuned[key] = c;
-            }
-        }
+        OwnerCfg c;
+        EP_TRY(gauss2_config(P, b, a, dt, st, tc, &c));
         TimedLaunch tl;
         char name[64];
         if (tc) {
@@ -1540,6 +1563,279 @@ ep_status persistent_steps(const ep_params& P, const AllPairsBufs& b, StageArgs 
         snprintf(name, sizeof(name), "k_shoot_mixed<%d,%d,1024> (G=%d)", P.dim, P.kernel, a.G);
         tl.record(name);
     }
+    return EP_OK;
+}
+
+// EP_DEVICE_MATCH=0 in the environment keeps Algorithm 1 on the host loop of ep_match
+// for the owner-computes shoot too (both compute the same result).
+bool device_match_enabled()
+{
+    const char* e = getenv("EP_DEVICE_MATCH");
+    return !(e && e[0] == '0');
+}
+
+namespace {
+
+// One step of Algorithm 1 after a shoot, in the loop body of the matching graph (one
+// CTA): the FP64 residual max_i |Y_i - Q_i(1)| (the arithmetic of k_max_abs_diff), the
+// stop tests in the order of the host loop of ep_match, the update p0 += h (Y - Q(1))
+// (k_momentum_update's arithmetic) and the loop condition; when the loop goes on, the
+// next shoot's start: its barrier words zeroed and (X, p0) loaded (k_load_state's
+// arithmetic).  The loop also ends when the shoot's barrier wait gave up (status
+// EP_ETIMEOUT) and, whatever the tests say, once maxit updates are done.
+struct GraphMatch {
+    const double* X;
+    const double* Y;
+    double* p0;
+    double* x;         // the FP64 state: positions (Q(1) after a shoot), then momenta
+    float4* Sx;        // the scaled FP32 stage input
+    double* Dx;        // FP64 stage copy, or null
+    const double* c0;  // centre of X
+    double s;          // coordinate scale
+    unsigned* bar;     // the shoot's barrier words: [0, 8) counters, [8] error flag
+    double* hist;      // [maxit + 1] or null
+    double* state;     // [3]: updates so far, last residual, status (-1 while running)
+    int n;
+    double eps;
+    double h;
+    int maxit;
+    int inexact;       // the inexact system (Sec. 6): stop when |h r|_inf < eps after an update
+    cudaGraphConditionalHandle loop;
+};
+
+__global__ void __launch_bounds__(1024) k_match_step(GraphMatch g)
+{
+    __shared__ double sm[32];
+    __shared__ int sbad, sgo;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    const size_t m = 2 * (size_t)g.n;
+    const double* Q = g.x;
+    double mx = 0.0;
+    int bad = 0;
+    for (size_t a = threadIdx.x; a < m; a += blockDim.x) {
+        const double r = g.Y[a] - Q[a];
+        if (!isfinite(r)) bad = 1;
+        mx = fmax(mx, fabs(r));
+    }
+    if (bad) sbad = 1;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, sm[k]);
+        const int k = (int)g.state[0];
+        const double res = sbad ? (double)NAN : t;
+        int status = -1;
+        if (*(volatile const int*)(g.bar + 8)) {
+            status = EP_ETIMEOUT;
+        } else {
+            if (g.hist) g.hist[k] = res;
+            if (sbad) status = EP_EDIVERGED;
+            else if (!g.inexact && res < g.eps) status = EP_OK;
+            else if (k >= g.maxit) status = EP_ENOTCONVERGED;
+        }
+        if (status < 0) {
+            g.state[0] = (double)(k + 1);
+            if (g.inexact && g.h * res < g.eps) status = EP_OK;
+        }
+        g.state[1] = res;
+        g.state[2] = (double)status;
+        sgo = status;
+    }
+    __syncthreads();
+    const int status = sgo;
+    if (status == EP_ETIMEOUT || status == EP_EDIVERGED || status == EP_ENOTCONVERGED ||
+        (status == EP_OK && !g.inexact)) {
+        if (threadIdx.x == 0) cudaGraphSetConditional(g.loop, 0u);
+        return;
+    }
+    // an update (the inexact system's stop comes after it)
+    for (size_t a = threadIdx.x; a < m; a += blockDim.x) g.p0[a] = fma(g.h, g.Y[a] - Q[a], g.p0[a]);
+    if (status == EP_OK) {
+        if (threadIdx.x == 0) cudaGraphSetConditional(g.loop, 0u);
+        return;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) g.bar[threadIdx.x] = 0u;
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+        const double qx = g.X[2 * (size_t)i], qy = g.X[2 * (size_t)i + 1];
+        const double px = g.p0[2 * (size_t)i], py = g.p0[2 * (size_t)i + 1];
+        g.x[2 * (size_t)i] = qx;
+        g.x[2 * (size_t)i + 1] = qy;
+        g.x[m + 2 * (size_t)i] = px;
+        g.x[m + 2 * (size_t)i + 1] = py;
+        g.Sx[i] = make_float4((float)((qx - g.c0[0]) * g.s), (float)((qy - g.c0[1]) * g.s), (float)px, (float)py);
+        if (g.Dx) {
+            g.Dx[4 * (size_t)i] = qx;
+            g.Dx[4 * (size_t)i + 1] = qy;
+            g.Dx[4 * (size_t)i + 2] = px;
+            g.Dx[4 * (size_t)i + 3] = py;
+        }
+    }
+    if (threadIdx.x == 0) cudaGraphSetConditional(g.loop, 1u);
+}
+
+template <int JL>
+ep_status owner_shoot_fits(int n, int G, bool* ok)
+{
+    constexpr int THREADS = owner_threads<JL>();
+    const size_t smem = owner_smem<THREADS, JL>();
+    auto fn = k_shoot_owner<THREADS, JL, false>;
+    static int res = -1;
+    if (res < 0) {
+        EP_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        EP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, THREADS, smem));
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        res = per_sm * di.sm_count;
+    }
+    *ok = G <= res && G <= kMaxPersistentCtas && n <= owner_chunk<JL>();
+    return EP_OK;
+}
+
+// The cooperative launch of one owner-computes shoot (as launch_owner, without zeroing
+// the barrier words or reading the error flag back: capturable into a graph).
+template <int JL>
+cudaError_t enqueue_owner_shoot(StageArgs a, const AllPairsBufs& b, int steps, cudaStream_t st)
+{
+    constexpr int THREADS = owner_threads<JL>();
+    const size_t smem = owner_smem<THREADS, JL>();
+    auto fn = k_shoot_owner<THREADS, JL, false>;
+    const float4* Sx = b.Sx;
+    float4* Sa = b.Sa;
+    float4* Sb = b.Sb;
+    unsigned* bar = b.bar;
+    int* err = b.err;
+    float4* rec = nullptr;
+    void* args[] = {&a, &Sx, &Sa, &Sb, &steps, &bar, &err, &rec};
+    return cudaLaunchCooperativeKernel((void*)fn, dim3(a.G), dim3(THREADS), args, smem, st);
+}
+
+}  // namespace
+
+size_t owner_match_bytes() { return sizeof(double) * 8; }
+
+// The matching graph: one while-loop node whose body is the host loop's iteration (the
+// owner-computes shoot, then k_match_step: residual, tests, update and the next
+// shoot's load), so that the whole of Algorithm 1 runs with no host round trip per
+// update.  The shoot kernel is
+// the one the host loop launches; the results are the host loop's bit for bit.
+ep_status owner_match(const ep_params& P, const AllPairsBufs& b, const double* X, const double* Y, double* p0,
+                      int maxit, double eps, double h, double* hist, double* scratch, cudaStream_t st, bool* done,
+                      double out[3])
+{
+    *done = false;
+    if (b.n == 0 || maxit < 0 || !(P.precision == EP_MIXED && P.dim == 2 && P.kernel == EP_GAUSS) ||
+        tc_enabled(P) || !allpairs_persistent_enabled() || !device_match_enabled())
+        return EP_OK;
+    const APConfig cfg = allpairs_config(b.n, P.dim, P.precision, P.kernel);
+    if (cfg.threads != 1024) return EP_OK;
+    const double dt = P.t1 / P.steps;
+    StageArgs a = base_args(P, b, cfg);
+    a.mode = MODE_RK4;
+    a.dt = dt;
+    a.dt_f = (float)dt;
+    a.Sx_w = b.Sx;
+    // the centre c0 of X (X does not change between shoots) and a loaded state, from
+    // which the tuner's trial shoots start
+    EP_TRY(allpairs_load(P, b, X, p0, st));
+    OwnerCfg c;
+    EP_TRY(gauss2_config(P, b, a, dt, st, false, &c));
+    if (c.JL == 0) return EP_OK;  // stream-K: the host loop
+    a.G = std::max(1, std::min(c.G, b.n));
+    bool fits = false;
+    if (c.JL == 1) EP_TRY(owner_shoot_fits<1>(b.n, a.G, &fits));
+    else if (c.JL == 4) EP_TRY(owner_shoot_fits<4>(b.n, a.G, &fits));
+    else if (c.JL == 8) EP_TRY(owner_shoot_fits<8>(b.n, a.G, &fits));
+    else EP_TRY(owner_shoot_fits<16>(b.n, a.G, &fits));
+    if (!fits) return EP_OK;
+    double* state = scratch;
+    EP_TRY_CUDA(cudaMemsetAsync(state, 0, sizeof(double) * 3, st));
+    const KernelScale ks = kernel_scale(P.kernel, P.sigma);
+
+    struct GraphGuard {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        ~GraphGuard()
+        {
+            if (x) cudaGraphExecDestroy(x);
+            if (g) cudaGraphDestroy(g);
+        }
+    } gg;
+    EP_TRY_CUDA(cudaGraphCreate(&gg.g, 0));
+    cudaGraphConditionalHandle loop;
+    EP_TRY_CUDA(cudaGraphConditionalHandleCreate(&loop, gg.g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    EP_TRY_CUDA(cudaGraphAddNode(&node, gg.g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    // the loop body, captured on a private stream of the device (capture needs a stream
+    // other than the legacy default one; the capture records and runs nothing, and it
+    // always ends, also on an error)
+    cudaStream_t cs = nullptr;
+    {
+        DeviceInfo di{};
+        EP_TRY(device_info(&di));
+        static std::mutex mu;
+        static std::map<int, cudaStream_t> streams;
+        std::lock_guard<std::mutex> lk(mu);
+        cudaStream_t& s0 = streams[di.device];
+        if (!s0) EP_TRY_CUDA(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+        cs = s0;
+        EP_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    }
+    cudaError_t ce = cudaSuccess;
+    {
+        if (c.JL == 1) ce = enqueue_owner_shoot<1>(a, b, P.steps, cs);
+        else if (c.JL == 4) ce = enqueue_owner_shoot<4>(a, b, P.steps, cs);
+        else if (c.JL == 8) ce = enqueue_owner_shoot<8>(a, b, P.steps, cs);
+        else ce = enqueue_owner_shoot<16>(a, b, P.steps, cs);
+    }
+    if (ce == cudaSuccess) {
+        const GraphMatch gm{X,    Y,     p0,   b.x, b.Sx, b.Dx, b.c0,           ks.s, b.bar,
+                            hist, state, b.n, eps, h,    maxit, P.inexact != 0.0, loop};
+        k_match_step<<<1, 1024, 0, cs>>>(gm);
+        ce = cudaGetLastError();
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce != cudaSuccess) return cuda_fail(ce, "matching graph capture");
+    EP_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
+    // the first shoot's start: (X, p0) is loaded (allpairs_load; the tuner's trials
+    // restore it), the barrier words are zeroed here, the later ones by k_match_step
+    EP_TRY_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(unsigned) * 9, st));
+    TimedLaunch tl;
+    if (tl.e0) EP_TRY_CUDA(cudaEventRecord(tl.e0, st));
+    EP_TRY_CUDA(cudaGraphLaunch(gg.x, st));
+    if (tl.e1) EP_TRY_CUDA(cudaEventRecord(tl.e1, st));
+    EP_TRY_CUDA(cudaMemcpyAsync(out, state, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    EP_TRY_CUDA(cudaStreamSynchronize(st));
+    const int k = (int)out[0];
+    const double res = out[1];
+    const int status = (int)out[2];
+    // the body ran once per shoot: k + 1 shoots, k after the inexact system's stop
+    const int shoots = (P.inexact != 0.0 && status == EP_OK) ? k : k + 1;
+    count_launch(2 * shoots);
+    if (status == EP_ETIMEOUT) {
+        bool d = false;
+        return finish_persistent(b, st, &d, a.G);
+    }
+    out[0] = res;
+    out[1] = (double)k;
+    out[2] = (double)status;
+    *done = true;
+    char name[80];
+    snprintf(name, sizeof(name), "matching graph: k_shoot_owner<%d,%d> (G=%d) x %d", c.JL == 8 ? 512 : 1024, c.JL,
+             a.G, shoots);
+    tl.record(name);
     return EP_OK;
 }
 

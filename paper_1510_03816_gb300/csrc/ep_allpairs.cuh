@@ -59,6 +59,17 @@ ep_status allpairs_steps(const ep_params& P, const AllPairsBufs& b, int steps, d
 ep_status allpairs_steps_rec(const ep_params& P, const AllPairsBufs& b, int steps, double dt, float4* rec,
                              double* drec, cudaStream_t st);
 
+// Algorithm 1 with M = h I on the momenta (Sec. 4) of a mixed-precision 2-D Gaussian
+// problem in one cooperative launch, when the shoot's (tuned) configuration is an
+// owner-computes kernel; *done = false otherwise, and the caller runs its host loop.
+// X, Y, p0: device, n x 2 row-major; p0 is updated in place.  hist: maxit + 1 device
+// doubles (the residual of every shoot) or null; scratch: owner_match_bytes() of device
+// memory; out (host) = {final residual, updates, status}.  Same results as the host loop.
+ep_status owner_match(const ep_params& P, const AllPairsBufs& b, const double* X, const double* Y, double* p0,
+                      int maxit, double eps, double h, double* hist, double* scratch, cudaStream_t st, bool* done,
+                      double out[3]);
+size_t owner_match_bytes();
+
 // Launch timing of the persistent shoot (ep_set_launch_timing): when on, the
 // launch functions record CUDA events around the cooperative launch.
 bool launch_timing_enabled();

@@ -533,15 +533,14 @@ static ep_status match_entry(const ep_params* params, int64_t n, const double* X
     }
     const bool hist_dev = info->hist && is_device_ptr(info->hist);
     Sizer z;
-    if (device_loop) {
-        z.add(match_device_bytes(n, P.dim, info->maxit, info->rule));
-        z.add(sizeof(double) * ((size_t)info->maxit + 1));
-    }
+    if (device_loop) z.add(match_device_bytes(n, P.dim, info->maxit, info->rule));
+    else z.add(owner_match_bytes());
+    z.add(sizeof(double) * ((size_t)info->maxit + 1));
     z.add(forward_bytes(P, n));
     plan_stage(z, X, m);
     plan_stage(z, Y, m);
     plan_stage(z, p0, m);
-    z.add(sizeof(double) * 3 * m);
+    for (int k = 0; k < 3; ++k) z.add(sizeof(double) * m);  // t0, t1, t2 (each carve is aligned)
     z.add(64);
     Arena* ar = nullptr;
     EP_TRY(arena_acquire(st, z.total, &ar));
@@ -585,11 +584,32 @@ static ep_status match_entry(const ep_params* params, int64_t n, const double* X
     int k = 0;
     double res = 0.0;
     double host_res[2];
-    for (;;) {
+    // the owner-computes 2-D Gaussian shoot runs the whole loop in one launch
+    bool on_device = false;
+    if (!f.cells) {
+        double* hist_d = hist_dev ? info->hist : nullptr;
+        if (info->hist && !hist_dev) hist_d = (double*)ar->carve(sizeof(double) * ((size_t)info->maxit + 1));
+        double* scratch = (double*)ar->carve(owner_match_bytes());
+        if (!scratch || (info->hist && !hist_d)) return set_error("ep_match: workspace plan too small"), EP_ENOMEM;
+        double out[3];
+        EP_TRY(owner_match(P, f.ap, sX.dev, sY.dev, sp.dev, info->maxit, info->eps, h, hist_d, scratch, st,
+                           &on_device, out));
+        if (on_device) {
+            res = out[0];
+            k = (int)out[1];
+            status = (ep_status)(int)out[2];
+            // shoots: k + 1, except the inexact system's stop after an update
+            const int shoots = (P.inexact != 0.0 && status == EP_OK) ? k : k + 1;
+            if (info->hist && !hist_dev)
+                EP_TRY_CUDA(cudaMemcpyAsync(info->hist, hist_d, sizeof(double) * (size_t)shoots,
+                                            cudaMemcpyDeviceToHost, st));
+        }
+    }
+    while (!on_device) {
         EP_TRY(forward_load(P, f, sX.dev, sp.dev, st));
         EP_TRY(forward_steps(P, f, P.steps, dt, st));
         count_launch();
-    k_max_abs_diff<<<1, 1024, 0, st>>>(sY.dev, Q1, m, scal);
+        k_max_abs_diff<<<1, 1024, 0, st>>>(sY.dev, Q1, m, scal);
         EP_TRY_CUDA(cudaMemcpyAsync(host_res, scal, sizeof host_res, cudaMemcpyDeviceToHost, st));
         EP_TRY_CUDA(cudaStreamSynchronize(st));
         const bool finite = host_res[1] == 0.0;

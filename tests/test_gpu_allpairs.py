@@ -228,3 +228,54 @@ def test_owner_kernel_default_forms_parity(n, monkeypatch):
     assert kname.startswith("k_shoot_owner<512,8>" if n >= 3648 else "k_shoot_owner<1024,16>"), kname
     rq, rp = o.shoot(pr.X, p0, pr.kernel, pr.sigma, 6)
     assert rel(q1, rq) < 1e-4 and rel(p1, rp) < 1e-4
+
+
+def _device_loop_case(name):
+    if name == "benchmark_cap":
+        pr = w.fourier_curve_warp()
+        return pr.X, pr.Y, ep.params(dim=2, kernel=pr.kernel, sigma=pr.sigma, steps=pr.steps, precision=ep.MIXED,
+                                     neigh=ep.ALLPAIRS), dict(h=0.0, eps=pr.eps, maxit=3)
+    if name == "ragged_converges":
+        pr = w.circle_to_ellipse(n=3700, kernel=ep.GAUSS, sigma=0.1, steps=20)
+        return pr.X, pr.Y, ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=20, precision=ep.MIXED,
+                                     neigh=ep.ALLPAIRS), dict(h=0.0, eps=2e-2, maxit=60)
+    if name == "1024_thread_form":
+        pr = w.circle_to_ellipse(n=1000, kernel=ep.GAUSS, sigma=0.1, steps=20)
+        return pr.X, pr.Y, ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=20, precision=ep.MIXED,
+                                     neigh=ep.ALLPAIRS), dict(h=0.0, eps=1e-6, maxit=4)
+    if name == "inexact_stop":
+        pr = w.circle_to_ellipse(n=1000, kernel=ep.GAUSS, sigma=0.1, steps=20)
+        return pr.X, pr.Y, ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=20, precision=ep.MIXED,
+                                     neigh=ep.ALLPAIRS, inexact=0.05), dict(h=0.0, eps=2e-3, maxit=200)
+    pr = w.circle_to_ellipse(n=500, kernel=ep.GAUSS, sigma=0.1, steps=10)  # diverges
+    return pr.X, pr.Y, ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.MIXED,
+                                 neigh=ep.ALLPAIRS), dict(h=60.0, eps=1e-6, maxit=40)
+
+
+@pytest.mark.parametrize("case", ["benchmark_cap", "ragged_converges", "1024_thread_form", "inexact_stop",
+                                  "diverges"])
+def test_device_matching_loop_equals_host_loop(case, monkeypatch):
+    """Algorithm 1 as one CUDA graph (a while-loop node over the load, the owner-computes
+    shoot and k_match_step: FP64 residual, stop tests and momentum update on the device)
+    against the host loop of ep_match over the same shoot kernel (EP_DEVICE_MATCH=0):
+    the same momenta, residual history, update count and status, bit for bit, in the
+    default launch configurations (EP_AUTOTUNE=0)."""
+    monkeypatch.setenv("EP_AUTOTUNE", "0")
+    X, Y, prm, kw = _device_loop_case(case)
+    ep.set_launch_timing(True)
+    try:
+        rd = ep.match(cuda(X), cuda(Y), prm, **kw)
+        _, kname = ep.last_launch()
+    finally:
+        ep.set_launch_timing(False)
+    assert kname.startswith("matching graph: k_shoot_owner<"), kname
+    monkeypatch.setenv("EP_DEVICE_MATCH", "0")
+    rh = ep.match(cuda(X), cuda(Y), prm, **kw)
+    assert (rd.status, rd.iters) == (rh.status, rh.iters)
+    assert rd.h == rh.h
+    assert rd.H == rh.H or (np.isnan(rd.H) and np.isnan(rh.H))
+    assert np.array_equal(rd.p0.cpu().numpy(), rh.p0.cpu().numpy())
+    assert np.array_equal(np.asarray(rd.hist), np.asarray(rh.hist), equal_nan=True)
+    expect = {"benchmark_cap": ep.ENOTCONVERGED, "ragged_converges": ep.OK, "1024_thread_form": ep.ENOTCONVERGED,
+              "inexact_stop": ep.OK, "diverges": ep.EDIVERGED}[case]
+    assert rd.status == expect, (case, rd.status, rd.iters, rd.hist[-3:])
