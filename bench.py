@@ -488,7 +488,7 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True, ba
             "gradients/s (extrapolated)",
             f"FP64 oracle exact RK4 adjoint at N=512, 10 steps, scaled by (N ratio)^2 x (step ratio) = {k:.0f}")
     # batched: 512 curve problems, n log-uniform in [32, 8192]; maxit = batched_maxit (200 is the
-    # stated configuration, ~90 s; the default run caps it at 10 for time)
+    # stated configuration, ~60 s; the default run caps it at 10 for time)
     bp = workloads.batched_curves()
     Xs = [torch.tensor(p.X, device=dev) for p in bp]
     Ys = [torch.tensor(p.Y, device=dev) for p in bp]
