@@ -460,6 +460,25 @@ def secondary(ep, workloads, dev, stream, peak_tflops, with_cpu: bool = True, ba
                                                          "(ncu, profiles/k_cell_sweep_jittered_grid_512.md)"},
                         "roofline_alu": _alu_roofline(acc_pairs * FLOPS_PER_PAIR_2D_TENT / (stage_us * 1e-6), peak_tflops,
                                                       f"{FLOPS_PER_PAIR_2D_TENT} flop per accepted pair")}
+    # the cell-list matching at its stated configuration: Algorithm 1 on the jittered grid,
+    # 100 RK4 steps, eps 1e-6, at most 200 updates, default gain
+    prm_m = ep.params(dim=2, kernel=ep.TENT, sigma=g.sigma, steps=100, precision=ep.MIXED, neigh=ep.CELLLIST)
+    Yg = torch.tensor(g.Y, device=dev)
+    ep.match(Xg, Yg, prm_m, h=0.0, eps=1e-6, maxit=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rm = ep.match(Xg, Yg, prm_m, h=0.0, eps=1e-6, maxit=200)
+    torch.cuda.synchronize()
+    dtm = time.perf_counter() - t0
+    mshoots = rm.iters + 1
+    out["cell_list_match"] = {"workload": "jittered_grid 512x512 (N=262144), tent sigma=sqrt(32/(pi N)), RK4 100 steps, "
+                                          "Algorithm 1 from p0=0, eps 1e-6, maxit 200, default gain",
+                              "seconds_per_match": dtm, "shoots": mshoots, "shoots_per_s": mshoots / dtm,
+                              "pair_interactions_per_s": acc_pairs * 400 * mshoots / dtm,
+                              "status": ep.STATUS_NAMES.get(rm.status, rm.status), "iters": rm.iters,
+                              "resid_inf": rm.resid,
+                              "roofline": {"bound": "latency", "note": "per stage as the cell_list row (its roofline); "
+                                           "the host loop adds one residual read-back per update"}}
     if with_cpu:
         rows = np.random.default_rng(0).choice(g.n, 1024, replace=False)
         out["cell_list"]["cpu_baseline"] = _oracle_sample(
