@@ -279,3 +279,19 @@ def test_device_matching_loop_equals_host_loop(case, monkeypatch):
     expect = {"benchmark_cap": ep.ENOTCONVERGED, "ragged_converges": ep.OK, "1024_thread_form": ep.ENOTCONVERGED,
               "inexact_stop": ep.OK, "diverges": ep.EDIVERGED}[case]
     assert rd.status == expect, (case, rd.status, rd.iters, rd.hist[-3:])
+
+
+@pytest.mark.parametrize("kernel,sigma,dim", [(ep.TENT, 0.1, 2), (ep.EXPCONE, 0.05, 2), (ep.GAUSS, 0.15, 3),
+                                              (ep.TENT, 0.2, 3)])
+def test_rhs_parity_packed_generic_multi_chunk(kernel, sigma, dim):
+    """The packed 512-thread pair stage of the tent, the exp-cone and 3-D (sources staged
+    in pairs, an odd count padded with a far, momentum-free source) over several staged
+    chunks with an odd tail: n = 4099, every row against the oracle within the RHS bound."""
+    n = 4099
+    q, p = cloud(n, dim, seed=11 + kernel + 3 * dim)
+    prm = ep.params(dim=dim, kernel=kernel, sigma=sigma, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    dq, dp = ep.rhs(cuda(q), cuda(p), prm)
+    rq, rp = o.rhs(q, p, kernel, sigma)
+    assert rel(dq, rq) < TOL[ep.MIXED]["rhs"]
+    keep = ~tent_boundary_rows(q, sigma) if kernel == ep.TENT else np.ones(n, bool)
+    assert rel(dp.cpu().numpy()[keep], rp[keep]) < TOL[ep.MIXED]["rhs"]
