@@ -215,6 +215,47 @@ __device__ __forceinline__ void load_rec_f32(const float4* Y, const float4* D, i
     }
 }
 
+// The Hessian-vector pair loop keeps its staged sources in pairs: float4 k of pair t
+// holds the components 2k and 2k+1 (in the order q, p, vq, vp) of sources 2t and
+// 2t+1, so one load gives the f32x2 operands of two sources, and both rows of a lane
+// take each record pair (measured 304 against 314 ms per N = 16384 3-D gradient for the
+// scalar loop; one row per pass measured no faster).  The differences are taken as
+// q_j - q_i and vq_j - vq_i, so the hq sums come out negated and their sign is
+// restored when they are added up.  An odd count is padded with a source far away and
+// without momentum or direction (position kPadCoord), whose terms are exactly zero.
+constexpr float kPadCoord = 1.0e18f;
+
+// The 4 DIM components (q, p, vq, vp) of source j, or of the padding source.
+template <int DIM>
+__device__ __forceinline__ void rec_comps(const float4* Y, const float4* D, int j, bool real, float (&c)[4 * DIM])
+{
+    RecF32<DIM> r;
+    if (real) {
+        load_rec_f32<DIM>(Y, D, j, r);
+    } else {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            r.q[k] = kPadCoord;
+            r.p[k] = r.vq[k] = r.vp[k] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        c[k] = r.q[k];
+        c[DIM + k] = r.p[k];
+        c[2 * DIM + k] = r.vq[k];
+        c[3 * DIM + k] = r.vp[k];
+    }
+}
+
+// Component c of both sources of a record pair.
+template <int DIM>
+__device__ __forceinline__ float2 pair_comp(const float4 (&S)[2 * DIM], int c)
+{
+    const float4& v = S[c >> 1];
+    return (c & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+}
+
 template <int DIM, int KER>
 __global__ void __launch_bounds__(kHvpThreads, 1) k_hvp_mixed(HvpArgs a)
 {
@@ -249,43 +290,76 @@ __global__ void __launch_bounds__(kHvpThreads, 1) k_hvp_mixed(HvpArgs a)
             for (int c = 0; c < DIM; ++c) hq[r][c] = hp[r][c] = 0.f;
         int nchunk = 0;
         bool first = true;
+        // broadcast operand pairs of the lane's two rows (differences taken as q_j - q_i)
+        float2 nq[2][DIM], nv[2][DIM], bp[2][DIM], bv[2][DIM];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                nq[r][c] = make_float2(-ri[r].q[c], -ri[r].q[c]);
+                nv[r][c] = make_float2(-ri[r].vq[c], -ri[r].vq[c]);
+                bp[r][c] = make_float2(ri[r].p[c], ri[r].p[c]);
+                bv[r][c] = make_float2(ri[r].vp[c], ri[r].vp[c]);
+            }
         for (int cj = j0; cj < j1; cj += kHvpChunk) {
             const int L = min(kHvpChunk, j1 - cj);
+            const int P = (L + 1) >> 1;
             __syncthreads();
-            for (int t = threadIdx.x; t < L * V; t += kHvpThreads) {
-                const int jj = t / V, k = t % V;
-                smem[(size_t)jj * 2 * V + k] = a.Y[(size_t)(cj + jj) * V + k];
-                smem[(size_t)jj * 2 * V + V + k] = a.Din[(size_t)(cj + jj) * V + k];
+            for (int t = threadIdx.x; t < P; t += kHvpThreads) {
+                const int j = cj + 2 * t;
+                float c0[4 * DIM], c1[4 * DIM];
+                rec_comps<DIM>(a.Y, a.Din, j, true, c0);
+                rec_comps<DIM>(a.Y, a.Din, j + 1, 2 * t + 1 < L, c1);
+#pragma unroll
+                for (int k = 0; k < 2 * DIM; ++k)
+                    smem[(size_t)t * 2 * DIM + k] = make_float4(c0[2 * k], c1[2 * k], c0[2 * k + 1], c1[2 * k + 1]);
             }
             __syncthreads();
-            const int ja = warp * L / W, jb = (warp + 1) * L / W;
-            for (int j = ja; j < jb; ++j) {
-                RecF32<DIM> rj;
-                load_rec_f32<DIM>(smem + (size_t)j * 2 * V, smem + (size_t)j * 2 * V + V, 0, rj);
+            const int pa = warp * P / W, pz = (warp + 1) * P / W;
+            float2 aq[2][DIM], ap[2][DIM];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) aq[r][c] = ap[r][c] = make_float2(0.f, 0.f);
+            for (int q = pa; q < pz; ++q) {
+                float4 S[2 * DIM];
+#pragma unroll
+                for (int k = 0; k < 2 * DIM; ++k) S[k] = smem[(size_t)q * 2 * DIM + k];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    float d[DIM], dv[DIM], r2 = 0.f, dd = 0.f, pa = 0.f, pb = 0.f;
+                    float2 d[DIM], dv[DIM];
+                    float2 r2 = make_float2(0.f, 0.f), dd = r2, pa2 = r2, pb2 = r2;
 #pragma unroll
                     for (int c = 0; c < DIM; ++c) {
-                        d[c] = ri[r].q[c] - rj.q[c];
-                        dv[c] = ri[r].vq[c] - rj.vq[c];
-                        r2 = fmaf(d[c], d[c], r2);
-                        dd = fmaf(d[c], dv[c], dd);
-                        pa = fmaf(ri[r].vp[c], rj.p[c], fmaf(ri[r].p[c], rj.vp[c], pa));
-                        pb = fmaf(ri[r].p[c], rj.p[c], pb);
+                        d[c] = __fadd2_rn(pair_comp<DIM>(S, c), nq[r][c]);
+                        dv[c] = __fadd2_rn(pair_comp<DIM>(S, 2 * DIM + c), nv[r][c]);
+                        r2 = __ffma2_rn(d[c], d[c], r2);
+                        dd = __ffma2_rn(d[c], dv[c], dd);
+                        pa2 = __ffma2_rn(bv[r][c], pair_comp<DIM>(S, DIM + c),
+                                         __ffma2_rn(bp[r][c], pair_comp<DIM>(S, 3 * DIM + c), pa2));
+                        pb2 = __ffma2_rn(bp[r][c], pair_comp<DIM>(S, DIM + c), pb2);
                     }
-                    float G, ph, ps;
-                    hfun_f32<KER>(r2, G, ph, ps);
-                    const float t = ph * dd;
-                    const float cd = fmaf(pa, ph, pb * ps * dd);
-                    const float cv = pb * ph;
+                    float2 G, ph, ps;
+                    hfun_f32<KER>(r2.x, G.x, ph.x, ps.x);
+                    hfun_f32<KER>(r2.y, G.y, ph.y, ps.y);
+                    const float2 t = __fmul2_rn(ph, dd);
+                    const float2 cd = __ffma2_rn(pa2, ph, __fmul2_rn(__fmul2_rn(pb2, ps), dd));
+                    const float2 cv = __fmul2_rn(pb2, ph);
 #pragma unroll
                     for (int c = 0; c < DIM; ++c) {
-                        hp[r][c] = fmaf(G, rj.vp[c], fmaf(t, rj.p[c], hp[r][c]));
-                        hq[r][c] = fmaf(cd, d[c], fmaf(cv, dv[c], hq[r][c]));
+                        ap[r][c] = __ffma2_rn(G, pair_comp<DIM>(S, 3 * DIM + c),
+                                              __ffma2_rn(t, pair_comp<DIM>(S, DIM + c), ap[r][c]));
+                        aq[r][c] = __ffma2_rn(cd, d[c], __ffma2_rn(cv, dv[c], aq[r][c]));
                     }
                 }
             }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int c = 0; c < DIM; ++c) {
+                    hq[r][c] -= aq[r][c].x + aq[r][c].y;
+                    hp[r][c] += ap[r][c].x + ap[r][c].y;
+                }
             // fold the lanes' FP32 blocks: every kHvpFoldChunks chunks and at the segment end
             if (++nchunk % kHvpFoldChunks != 0 && cj + kHvpChunk < j1) continue;
             __syncthreads();
