@@ -93,6 +93,18 @@ struct Rk4 {
     }
 };
 
+// Position (scaled units) of the padding particle of an odd particle count in the
+// packed source-pair records: its kernel value is exactly zero at every target.
+constexpr float kPadCoord = 1.0e18f;
+
+// Component c (q then p) of both particles of a staged record pair.
+template <int DIM>
+__device__ __forceinline__ float2 flow_comp(const float4 (&S)[DIM], int c)
+{
+    const float4& v = S[c >> 1];
+    return (c & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+}
+
 // One CTA: kFlowTile targets (lane l of every warp holds targets l and l + 32);
 // the 8 warps split each staged chunk of particles, their partial velocities are
 // summed in shared memory, and warp 0 applies the RK4 stage and publishes the
@@ -135,38 +147,71 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_mixed(FlowArgs a)
                 y[r][c] = s_y[lane + 32 * r][c];
                 u[r][c] = 0.0f;
             }
+        // the targets' negated positions as broadcast pairs; the particle records are
+        // staged in source pairs (float4 k of a pair holds components 2k and 2k+1, in
+        // the order q, p, of both sources), so one load gives the f32x2 operands of
+        // two particles; an odd count is padded with a particle far away and without
+        // momentum, whose terms are exactly zero
+        constexpr int PV = DIM;  // float4 per source pair
+        float2 ny[kFlowRT][DIM], u2[kFlowRT][DIM];
+#pragma unroll
+        for (int r = 0; r < kFlowRT; ++r)
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                ny[r][c] = make_float2(-y[r][c], -y[r][c]);
+                u2[r][c] = make_float2(0.0f, 0.0f);
+            }
         for (int cj = 0; cj < n; cj += kFlowChunk) {
             const int L = min(kFlowChunk, n - cj);
+            const int P = (L + 1) >> 1;
             if (cj > 0) __syncthreads();
-            for (int t = threadIdx.x; t < L * V; t += kFlowThreads) sm[t] = __ldg(copy + (size_t)cj * V + t);
-            __syncthreads();
-            const int ja = warp * L / W, jb = (warp + 1) * L / W;
-#pragma unroll 2
-            for (int j = ja; j < jb; ++j) {
-                float qj[DIM], pj[DIM];
+            for (int t = threadIdx.x; t < P; t += kFlowThreads) {
+                const int j = cj + 2 * t;
+                const bool two = 2 * t + 1 < L;
+                float c0[2 * DIM], c1[2 * DIM];
                 if constexpr (DIM == 2) {
-                    const float4 v = sm[j];
-                    qj[0] = v.x; qj[1] = v.y; pj[0] = v.z; pj[1] = v.w;
+                    const float4 v0 = __ldg(copy + j);
+                    const float4 v1 = two ? __ldg(copy + j + 1) : make_float4(kPadCoord, kPadCoord, 0.f, 0.f);
+                    c0[0] = v0.x; c0[1] = v0.y; c0[2] = v0.z; c0[3] = v0.w;
+                    c1[0] = v1.x; c1[1] = v1.y; c1[2] = v1.z; c1[3] = v1.w;
                 } else {
-                    const float4 v0 = sm[2 * j], v1 = sm[2 * j + 1];
-                    qj[0] = v0.x; qj[1] = v0.y; qj[2] = v0.z;
-                    pj[0] = v1.x; pj[1] = v1.y; pj[2] = v1.z;
+                    const float4 q0 = __ldg(copy + 2 * (size_t)j), p0 = __ldg(copy + 2 * (size_t)j + 1);
+                    const float4 q1 = two ? __ldg(copy + 2 * (size_t)j + 2) : make_float4(kPadCoord, kPadCoord, kPadCoord, 0.f);
+                    const float4 p1 = two ? __ldg(copy + 2 * (size_t)j + 3) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    c0[0] = q0.x; c0[1] = q0.y; c0[2] = q0.z; c0[3] = p0.x; c0[4] = p0.y; c0[5] = p0.z;
+                    c1[0] = q1.x; c1[1] = q1.y; c1[2] = q1.z; c1[3] = p1.x; c1[4] = p1.y; c1[5] = p1.z;
                 }
 #pragma unroll
+                for (int k = 0; k < PV; ++k)
+                    sm[(size_t)t * PV + k] = make_float4(c0[2 * k], c1[2 * k], c0[2 * k + 1], c1[2 * k + 1]);
+            }
+            __syncthreads();
+            const int pa = warp * P / W, pz = (warp + 1) * P / W;
+#pragma unroll 2
+            for (int q = pa; q < pz; ++q) {
+                float4 S[PV];
+#pragma unroll
+                for (int k = 0; k < PV; ++k) S[k] = sm[(size_t)q * PV + k];
+#pragma unroll
                 for (int r = 0; r < kFlowRT; ++r) {
-                    float r2 = 0.0f;
+                    float2 r2 = make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int c = 0; c < DIM; ++c) {
-                        const float d = y[r][c] - qj[c];
-                        r2 = fmaf(d, d, r2);
+                        const float2 d = __fadd2_rn(flow_comp<DIM>(S, c), ny[r][c]);
+                        r2 = __ffma2_rn(d, d, r2);
                     }
-                    float G, w;
-                    kfun_f32<KER>(r2, G, w);
+                    float2 G, w;
+                    kfun_f32<KER>(r2.x, G.x, w.x);
+                    kfun_f32<KER>(r2.y, G.y, w.y);
 #pragma unroll
-                    for (int c = 0; c < DIM; ++c) u[r][c] = fmaf(G, pj[c], u[r][c]);
+                    for (int c = 0; c < DIM; ++c) u2[r][c] = __ffma2_rn(G, flow_comp<DIM>(S, DIM + c), u2[r][c]);
                 }
             }
         }
+#pragma unroll
+        for (int r = 0; r < kFlowRT; ++r)
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) u[r][c] = u2[r][c].x + u2[r][c].y;
 #pragma unroll
         for (int r = 0; r < kFlowRT; ++r)
 #pragma unroll
