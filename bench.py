@@ -82,7 +82,8 @@ def parse():
     ap.add_argument("--profile-rk4-steps", type=int, default=0,
                     help="with --profile: RK4 steps per shoot (0 = the workload's 100), for short captures")
     ap.add_argument("--profile-row", default="", choices=["", "cell_list", "batched", "tangent", "match_fp64",
-                                                           "velocity", "adjoint", "newton", "newton_mixed"],
+                                                           "velocity", "adjoint", "newton", "newton_mixed",
+                                                           "rhs", "flow"],
                     help="run one small case of that secondary row (for ncu captures); no JSON line")
     return ap.parse_args()
 
@@ -96,7 +97,9 @@ def profile_row(name: str) -> None:
     velocity   the same with the velocity update, 3 updates (factored G(X) inside k_match_fp64)
     adjoint    one gradient of the N = 16384 3-D star-surface workload (100 steps, checkpoints every 10)
     newton     the N = 64 circle -> ellipse Newton matching, FP64, 1 update (k_jac_fp64, k_lu_solve)
-    newton_mixed  the same in mixed precision (k_jac_mixed)"""
+    newton_mixed  the same in mixed precision (k_jac_mixed)
+    rhs        one mixed-precision RHS of the N = 4096 Fourier-curve workload (k_stage_mixed), twice
+    flow       a 64 x 64 grid carried by the N = 4096 Fourier-curve shoot, 5 RK4 steps (k_flow_mixed)"""
     import torch
     from paper_1510_03816_gb300 import ep, workloads
 
@@ -108,6 +111,17 @@ def profile_row(name: str) -> None:
         prm = ep.params(dim=2, kernel=c.kernel, sigma=c.sigma, steps=c.steps, precision=prec, neigh=ep.ALLPAIRS)
         ep.match(torch.tensor(c.X, device=dev), torch.tensor(c.Y, device=dev), prm, h=1.0, eps=0.0, maxit=1,
                  rule=ep.RULE_NEWTON)
+    elif name in ("rhs", "flow"):
+        f = workloads.fourier_curve_warp(steps=5)
+        X = torch.tensor(f.X, device=dev)
+        p = 0.002 * (torch.tensor(f.Y, device=dev) - X)
+        prm = ep.params(dim=2, kernel=f.kernel, sigma=f.sigma, steps=f.steps, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+        if name == "rhs":
+            for _ in range(2):
+                ep.rhs(X, p, prm)
+        else:
+            g = torch.linspace(0.0, 1.0, 64, device=dev, dtype=torch.float64)
+            ep.flow(X, p, torch.cartesian_prod(g, g), prm)
     elif name == "adjoint":
         a3 = workloads.star_surface_3d()
         X3, Y3, p3 = (torch.tensor(v, device=dev) for v in (a3.X, a3.Y, a3.p0))
