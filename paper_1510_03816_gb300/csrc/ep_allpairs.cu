@@ -101,9 +101,9 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
             // source far away and without momentum, whose terms are exactly zero.  Both
             // rows of the lane take each record pair; the differences are q_j - q_i, so
             // the momentum sums come out negated and their sign is restored at the fold.
-            // Measured faster than the 1024-thread scalar loop for every kernel (3-D
-            // Gaussian at N = 16384: 171 against 185 us per stage; 2-D tent at N = 4096:
-            // 16.8 against 17.9 us; 3-D tent: 20.6 against 23.5 us; 768 threads: slower)
+            // Measured against the 1024-thread scalar loop: 3-D Gaussian at N = 16384 171
+            // against 185 us per stage, 2-D tent at N = 4096 16.8 against 17.9 us, 3-D
+            // tent 20.6 against 23.5 us, 2-D exp-cone the same (17.7 us); 768 threads: slower)
             constexpr int PV = DIM == 2 ? 2 : 3;  // float4 per source pair
             float2 nq[2][DIM], pb[2][DIM];
 #pragma unroll
