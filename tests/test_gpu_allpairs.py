@@ -295,3 +295,38 @@ def test_rhs_parity_packed_generic_multi_chunk(kernel, sigma, dim):
     assert rel(dq, rq) < TOL[ep.MIXED]["rhs"]
     keep = ~tent_boundary_rows(q, sigma) if kernel == ep.TENT else np.ones(n, bool)
     assert rel(dp.cpu().numpy()[keep], rp[keep]) < TOL[ep.MIXED]["rhs"]
+
+
+@pytest.mark.parametrize("variant", ["maxit0", "no_hist", "host_arrays"])
+def test_device_matching_loop_edge_calls(variant, monkeypatch):
+    """The matching graph at its edges: a single shoot (maxit = 0), no residual history
+    requested, and host (numpy) arrays staged through the C ABI; momenta, status and
+    update count equal the host loop's bit for bit."""
+    monkeypatch.setenv("EP_AUTOTUNE", "0")
+    pr = w.circle_to_ellipse(n=1000, kernel=ep.GAUSS, sigma=0.1, steps=10)
+    prm = ep.params(dim=2, kernel=ep.GAUSS, sigma=0.1, steps=10, precision=ep.MIXED, neigh=ep.ALLPAIRS)
+    kw = dict(h=0.0, eps=1e-6, maxit=0 if variant == "maxit0" else 3, hist=variant != "no_hist")
+
+    def run():
+        if variant == "host_arrays":
+            r = ep.match(np.asarray(pr.X), np.asarray(pr.Y), prm, **kw)
+            return r, np.asarray(r.p0)
+        r = ep.match(cuda(pr.X), cuda(pr.Y), prm, **kw)
+        return r, r.p0.cpu().numpy()
+
+    ep.set_launch_timing(True)
+    try:
+        rd, pd = run()
+        _, kname = ep.last_launch()
+    finally:
+        ep.set_launch_timing(False)
+    assert kname.startswith("matching graph: k_shoot_owner<"), kname
+    monkeypatch.setenv("EP_DEVICE_MATCH", "0")
+    rh, ph = run()
+    assert (rd.status, rd.iters, rd.resid) == (rh.status, rh.iters, rh.resid)
+    assert rd.status == ep.ENOTCONVERGED and rd.iters == kw["maxit"]
+    assert np.array_equal(pd, ph)
+    if kw["hist"]:
+        assert np.array_equal(np.asarray(rd.hist), np.asarray(rh.hist)) and len(rd.hist) == kw["maxit"] + 1
+    else:
+        assert rd.hist is None and rh.hist is None
