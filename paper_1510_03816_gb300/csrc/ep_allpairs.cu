@@ -1901,12 +1901,13 @@ ep_status owner_match(const ep_params& P, const AllPairsBufs& b, const double* X
     // other than the legacy default one; the capture records and runs nothing, and it
     // always ends, also on an error)
     cudaStream_t cs = nullptr;
+    // one capture at a time: calls from several host threads share the capture streams
+    static std::mutex capture_mu;
+    std::unique_lock<std::mutex> capture_lock(capture_mu);
     {
         DeviceInfo di{};
         EP_TRY(device_info(&di));
-        static std::mutex mu;
         static std::map<int, cudaStream_t> streams;
-        std::lock_guard<std::mutex> lk(mu);
         cudaStream_t& s0 = streams[di.device];
         if (!s0) EP_TRY_CUDA(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
         cs = s0;
@@ -1927,6 +1928,7 @@ ep_status owner_match(const ep_params& P, const AllPairsBufs& b, const double* X
     }
     cudaGraph_t captured = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(cs, &captured);
+    capture_lock.unlock();
     if (ce == cudaSuccess) ce = ee;
     if (ce != cudaSuccess) return cuda_fail(ce, "matching graph capture");
     EP_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
