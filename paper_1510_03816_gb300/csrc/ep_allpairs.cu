@@ -93,7 +93,8 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                 for (int c = 0; c < DIM; ++c) { qi[r][c] = 0.0f; pi[r][c] = 0.0f; }
             }
         }
-        if constexpr (THREADS == 512) {
+        static_assert(THREADS == 512, "the generic pair stage runs in its 512-thread packed form");
+        {
             // packed form (the 512-thread kernels): the staged sources are kept in pairs,
             // one float4 holding the positions of sources 2p and 2p+1 (2-D: x, x, y, y;
             // 3-D: x, x, y, y then z, z, px, px) and the next their momenta, so one load
@@ -188,7 +189,8 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                     }
                 }
                 if (++nchunk2 % FOLD != 0 && cj + kChunk < j1) continue;
-                // fold as below; the halves are added and the negated sums' sign restored
+                // fold: the lanes' pair halves added (the negated sums' sign restored) -> shared
+                // memory [W][6][64] -> double-FP32 over the warps -> the FP64 accumulator
                 __syncthreads();
                 float* red = reinterpret_cast<float*>(smem);
                 constexpr int kNeg = DIM == 2 ? 2 : 3;  // first component summed negated
@@ -210,79 +212,6 @@ __device__ __forceinline__ void stage_pairs(const StageArgs& a, float4* smem, in
                     if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, dd_to_double(dd_add(sum, make_float2(0.f, 0.f))));
                 }
             }
-        } else {
-        // the lane's two particles' sums, FP32 over FOLD staged chunks, then folded
-        float acc[2][kKWidth];
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-            for (int t = 0; t < kKWidth; ++t) acc[r][t] = 0.0f;
-        int nchunk = 0;
-        for (int cj = j0; cj < j1; cj += kChunk) {
-            const int L = min(kChunk, j1 - cj);
-            __syncthreads();
-            for (int t = threadIdx.x; t < L * V; t += THREADS) smem[t] = __ldcg(a.S_in + (size_t)cj * V + t);
-            __syncthreads();
-            const int ja = warp * L / W, jb = (warp + 1) * L / W;
-#pragma unroll 4
-            for (int j = ja; j < jb; ++j) {
-                if constexpr (DIM == 2) {
-                    const float4 v = smem[j];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const float dx = qi[r][0] - v.x, dy = qi[r][1] - v.y;
-                        const float r2 = fmaf(dx, dx, dy * dy);
-                        float G, w;
-                        kfun_f32<KER>(r2, G, w);
-                        acc[r][0] = fmaf(G, v.z, acc[r][0]);
-                        acc[r][1] = fmaf(G, v.w, acc[r][1]);
-                        const float tx = w * dx, ty = w * dy;
-                        acc[r][2] = fmaf(tx, v.z, acc[r][2]);
-                        acc[r][3] = fmaf(tx, v.w, acc[r][3]);
-                        acc[r][4] = fmaf(ty, v.z, acc[r][4]);
-                        acc[r][5] = fmaf(ty, v.w, acc[r][5]);
-                    }
-                } else {
-                    const float4 v0 = smem[2 * j], v1 = smem[2 * j + 1];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const float dx = qi[r][0] - v0.x, dy = qi[r][1] - v0.y, dz = qi[r][2] - v0.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        float G, w;
-                        kfun_f32<KER>(r2, G, w);
-                        acc[r][0] = fmaf(G, v1.x, acc[r][0]);
-                        acc[r][1] = fmaf(G, v1.y, acc[r][1]);
-                        acc[r][2] = fmaf(G, v1.z, acc[r][2]);
-                        const float pp = fmaf(pi[r][0], v1.x, fmaf(pi[r][1], v1.y, pi[r][2] * v1.z));
-                        const float c = w * pp;
-                        acc[r][3] = fmaf(c, dx, acc[r][3]);
-                        acc[r][4] = fmaf(c, dy, acc[r][4]);
-                        acc[r][5] = fmaf(c, dz, acc[r][5]);
-                    }
-                }
-            }
-            if (++nchunk % FOLD != 0 && cj + kChunk < j1) continue;
-            // fold: warps' partials -> shared memory [W][6][64] -> double-FP32 over the warps ->
-            // the FP64 accumulator (exact conversion)
-            __syncthreads();
-            float* red = reinterpret_cast<float*>(smem);
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int t = 0; t < kKWidth; ++t) {
-                    red[(warp * kKWidth + t) * kTileI + lane + 32 * r] = acc[r][t];
-                    acc[r][t] = 0.0f;
-                }
-            __syncthreads();
-            for (int t = threadIdx.x; t < kKWidth * kTileI; t += THREADS) {
-                const int k = t / kTileI, il = t % kTileI;
-                float2 sum = make_float2(0.0f, 0.0f);
-#pragma unroll 8
-                for (int w2 = 0; w2 < W; ++w2) dd_acc(sum, red[(w2 * kKWidth + k) * kTileI + il]);
-                const int i = b * kTileI + il;
-                if (i < n) atomicAdd(a.K + (size_t)i * kKWidth + k, dd_to_double(dd_add(sum, make_float2(0.f, 0.f))));
-            }
-        }
         }
         if constexpr (LAST) {
             __threadfence();
@@ -1126,8 +1055,8 @@ ep_status launch_stage(const ep_params& P, const StageArgs& a, int threads, cuda
 {
 #define EP_MIXED_CASE(D, K)                                                       \
     if (P.dim == D && P.kernel == K) {                                            \
-        if (threads >= 512) return launch_mixed<D, K, 512>(a, st);                \
-        return launch_mixed<D, K, 256>(a, st);                                    \
+        (void)threads;                                                            \
+        return launch_mixed<D, K, 512>(a, st);                                    \
     }
 #define EP_FP64_CASE(D, K) \
     if (P.dim == D && P.kernel == K) return launch_fp64<D, K>(a, P.sigma, st);
